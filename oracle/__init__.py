@@ -1,0 +1,222 @@
+"""Plain FP64 CPU oracle of the STEV solver (arXiv:1905.09395), via ctypes.
+
+TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
+baseline leg may use it; the product path never does.  It imports nothing
+from the product package; a mechanism is any object carrying the table
+attributes (mol_weight, nasa7, t_range, rxn_ptr, rxn_species, rxn_nu, A, beta,
+Ea, reversible).
+
+The arithmetic lives in stev_oracle.c (plain C, one cell at a time, every
+function citing the equation it follows); this module only marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stev_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+DEFAULT_OPTS = dict(
+    y_step_max=1e-3,   # Y_step^max (Eq. 3), mass fraction per step
+    delta_max=0.01,    # delta^max (Eq. 4)
+    alpha=1e-5,        # Eq. 7
+    dft_n=13,          # N, the stored history length (Sec. 2.3)
+    dft_hi_first=4,    # n, first high-frequency bin (Eq. 10)
+    tol_ring=0.5,      # Tol_ring (Eq. 12)
+    tol_freq=1e-6,     # Tol_freq (Eq. 12), mol/m^3
+    r_fac=2.0,         # r_fac (Eq. 12)
+    rof_min=1e-30,     # keeps rOF > 0
+    max_iters=200000,  # per-cell cap
+    dft_on=1,
+)
+
+CELL_OK, CELL_MAXITER, CELL_NONFINITE, CELL_TRANGE = 0, 1, 2, 3
+
+
+class _Mech(ctypes.Structure):
+    _fields_ = [
+        ("n_species", ctypes.c_int), ("n_reactions", ctypes.c_int),
+        ("mol_weight", ctypes.c_void_p), ("nasa7", ctypes.c_void_p),
+        ("t_range", ctypes.c_void_p), ("rxn_ptr", ctypes.c_void_p),
+        ("rxn_species", ctypes.c_void_p), ("rxn_nu", ctypes.c_void_p),
+        ("A", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("Ea", ctypes.c_void_p),
+        ("reversible", ctypes.c_void_p),
+    ]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [
+        ("y_step_max", ctypes.c_double), ("delta_max", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("dft_n", ctypes.c_int), ("dft_hi_first", ctypes.c_int),
+        ("tol_ring", ctypes.c_double), ("tol_freq", ctypes.c_double),
+        ("r_fac", ctypes.c_double), ("rof_min", ctypes.c_double),
+        ("max_iters", ctypes.c_int), ("dft_on", ctypes.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        _lib.oracle_thermo.argtypes = [P, ctypes.c_double, P, P, P]
+        _lib.oracle_rates.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P, P]
+        _lib.oracle_step_size.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double]
+        _lib.oracle_step_size.restype = ctypes.c_double
+        _lib.oracle_dft_mag.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        _lib.oracle_dft_mag.restype = ctypes.c_double
+        _lib.oracle_ring_update.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double]
+        _lib.oracle_ring_update.restype = ctypes.c_double
+        _lib.oracle_solve_cell_trace.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P,
+                                                 ctypes.c_double, P, P, P, ctypes.c_int, P, P, P]
+        _lib.oracle_solve_cell_trace.restype = ctypes.c_int
+        _lib.oracle_solve.argtypes = [P, P, ctypes.c_long, P, P, P, ctypes.c_double, P, P, P, P,
+                                      ctypes.c_int]
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class OracleMechanism:
+    """Holds contiguous copies of a mechanism's tables and the C struct."""
+
+    def __init__(self, mech):
+        self.S = int(np.asarray(mech.mol_weight).shape[0])
+        self.R = int(np.asarray(mech.A).shape[0])
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        self._arrays = dict(
+            mol_weight=f64(mech.mol_weight), nasa7=f64(mech.nasa7), t_range=f64(mech.t_range),
+            rxn_ptr=np.ascontiguousarray(mech.rxn_ptr, dtype=np.int32),
+            rxn_species=np.ascontiguousarray(mech.rxn_species, dtype=np.int32),
+            rxn_nu=f64(mech.rxn_nu), A=f64(mech.A), beta=f64(mech.beta), Ea=f64(mech.Ea),
+            reversible=np.ascontiguousarray(mech.reversible, dtype=np.uint8))
+        a = self._arrays
+        self.struct = _Mech(self.S, self.R, *(_ptr(a[k]) for k in (
+            "mol_weight", "nasa7", "t_range", "rxn_ptr", "rxn_species", "rxn_nu", "A", "beta",
+            "Ea", "reversible")))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def make_opts(**overrides) -> _Opts:
+    d = dict(DEFAULT_OPTS)
+    for k, v in overrides.items():
+        if k not in d:
+            raise KeyError(k)
+        d[k] = v
+    return _Opts(float(d["y_step_max"]), float(d["delta_max"]), float(d["alpha"]),
+                 int(d["dft_n"]), int(d["dft_hi_first"]), float(d["tol_ring"]),
+                 float(d["tol_freq"]), float(d["r_fac"]), float(d["rof_min"]),
+                 int(d["max_iters"]), int(d["dft_on"]))
+
+
+def _om(mech) -> OracleMechanism:
+    return mech if isinstance(mech, OracleMechanism) else OracleMechanism(mech)
+
+
+def thermo(mech, T: float):
+    """(cp/R, H/RT, S/R) per species at T (Eqs. 15-16)."""
+    om = _om(mech)
+    cp, h, s = (np.zeros(om.S) for _ in range(3))
+    lib().oracle_thermo(om.ref, float(T), _ptr(cp), _ptr(h), _ptr(s))
+    return cp, h, s
+
+
+def rates(mech, T: float, P: float, Y, rOF=None, **opts):
+    """Right-hand side of the cell ODE: dict(qraw, wdot, dYdt, dTdt)."""
+    om = _om(mech)
+    o = make_opts(**opts)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    rOF = np.ones(om.R) if rOF is None else np.ascontiguousarray(rOF, dtype=np.float64)
+    q, w, dy = np.zeros(om.R), np.zeros(om.S), np.zeros(om.S)
+    dT = ctypes.c_double(0.0)
+    lib().oracle_rates(om.ref, ctypes.byref(o), float(T), float(P), _ptr(Y), _ptr(rOF), _ptr(q),
+                       _ptr(w), _ptr(dy), ctypes.addressof(dT))
+    return dict(qraw=q, wdot=w, dYdt=dy, dTdt=dT.value)
+
+
+def step_size(Y, dYdt, t_f, y_step_max=DEFAULT_OPTS["y_step_max"],
+              delta_max=DEFAULT_OPTS["delta_max"]) -> float:
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    dYdt = np.ascontiguousarray(dYdt, dtype=np.float64)
+    return lib().oracle_step_size(len(Y), _ptr(Y), _ptr(dYdt), float(t_f), float(y_step_max),
+                                  float(delta_max))
+
+
+def dft_mag(x, j: int) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().oracle_dft_mag(_ptr(x), len(x), int(j))
+
+
+def ring_update(x, rOF: float, **opts) -> float:
+    d = dict(DEFAULT_OPTS)
+    d.update(opts)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().oracle_ring_update(_ptr(x), len(x), int(d["dft_hi_first"]), float(rOF),
+                                    float(d["tol_ring"]), float(d["tol_freq"]),
+                                    float(d["r_fac"]), float(d["rof_min"]))
+
+
+def solve_cell_trace(mech, T0: float, P: float, Y0, dt: float, trace_cap: int = 100000, **opts):
+    """One cell with its per-step trace (h, T, Y at the start of each step)."""
+    om = _om(mech)
+    o = make_opts(**opts)
+    Y0 = np.ascontiguousarray(Y0, dtype=np.float64)
+    Yo = np.zeros(om.S)
+    To = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    cap = max(int(trace_cap), 1)
+    th, tT, tY = np.zeros(cap), np.zeros(cap), np.zeros((cap, om.S))
+    st = lib().oracle_solve_cell_trace(om.ref, ctypes.byref(o), float(T0), float(P), _ptr(Y0),
+                                       float(dt), ctypes.addressof(To), _ptr(Yo),
+                                       ctypes.addressof(it), int(trace_cap), _ptr(th), _ptr(tT),
+                                       _ptr(tY))
+    n = min(it.value, int(trace_cap))
+    return dict(T=To.value, Y=Yo, iters=it.value, status=st, h=th[:n], T_trace=tT[:n],
+                Y_trace=tY[:n])
+
+
+def solve(mech, T, P, Y, dt: float, n_threads: Optional[int] = None, **opts):
+    """All cells: returns (T_out, Y_out, iters, status)."""
+    om = _om(mech)
+    o = make_opts(**opts)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(len(T), om.S)
+    n = len(T)
+    To, Yo = np.zeros(n), np.zeros((n, om.S))
+    iters, status = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.uint8)
+    if n == 0:
+        return To, Yo, iters, status
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    n_threads = max(1, min(int(n_threads), n))
+    lib().oracle_solve(om.ref, ctypes.byref(o), n, _ptr(T), _ptr(P), _ptr(Y), float(dt), _ptr(To),
+                       _ptr(Yo), _ptr(iters), _ptr(status), n_threads)
+    return To, Yo, iters, status
