@@ -1,0 +1,328 @@
+"""Benchmark of the STEV hot path: cell-solves/s at 1,048,576 cells.
+
+One step = one stev_solve of every cell of the workload (32 species / 150
+reactions, T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), dt = 1e-3 s),
+i.e. one pass of the whole hot path over one batch.  Cells are independent,
+so with N GPUs every rank solves its own batch (weak scaling, no collective on
+the data path; a barrier only brackets the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+
+Smaller cases for profiling: --cells N and --max-iters K shrink the workload
+(the line then names them in config).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-solves/s at 1M cells: mixed+MLP vs plain FP64 STEV, 1 B300; p99 latency"
+UNIT = "cell-solves/s"
+N_CELLS = 1 << 20
+
+# FP64-pipe cost of CUDA's exp() and log() in DFMA-equivalents, measured on
+# B300 by csrc/alu_peaks.cu (dfma 1.667/clk/SM, exp 0.104, log 0.055, div 0.222)
+EXP_OPS, LOG_OPS, DIV_OPS = 16.0, 30.0, 7.5
+# FP64 pipe peak: 1.667 DFMA/clk/SM x 148 SMs at the probe's 1919 MHz under load
+FP64_PEAK_OPS = 4.733e11
+
+
+def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
+    """Algorithmic FP64 work of one STEV iteration of one cell, in DFMA-equivalents.
+
+    Counted from the method (not from the kernel): per species thermo (cp 4,
+    H/RT 6, G/RT 7 ops), mixture and cp sums (3), gamma and concentration
+    (3 + 1 division), production-rate bookkeeping (dY/dt 2, H.wdot 1),
+    limiter (4 + 1 division amortised by the min), Euler (1); per reaction
+    ln kf (2) + exp, reactant and product products (2), dG (3), ln kr (2) +
+    exp, net rate and rOF (2); one FMA per stoichiometric entry; per
+    reversible reaction the history entry (1), the N-point window sum of
+    Eq. 9's D0 (N-1) and the rOF update (3); per cell-step log T, 1/T and the
+    scalar updates (~12 ops + log + 2 divisions)."""
+    species = S * (4 + 6 + 7 + 3 + 3 + DIV_OPS + 3 + 4 + 1)
+    reactions = R * (2 + 2 + 3 + 2 + 2 + 2 * EXP_OPS)
+    gather = nnz
+    dft = Rrev * (1 + 12 + 3)
+    scalars = 12 + LOG_OPS + 3 * DIV_OPS
+    return species + reactions + gather + dft + scalars
+
+
+def workload(n_cells: int, rank: int = 0):
+    from paper_1905_09395_b300 import synth
+    return synth.scale_case(n_cells, seed=1 + 1000 * rank)
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" +
+                                      self.FIELDS, "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.25)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 4 + k and r[4 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus: int):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def cpu_baseline(mech, T, P, Y, dt, target_s: float = 15.0, **opts):
+    """The oracle as it stands on this host's cores, on a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n = max(cores, 8)
+    t0 = time.time()
+    oracle.solve(mech, T[:n], P[:n], Y[:n], dt, n_threads=cores, **opts)
+    first = time.time() - t0
+    # grow the sample to ~target_s of work (cells are independent and alike)
+    n2 = int(min(len(T), max(n, n * target_s / max(first, 1e-3))))
+    if n2 > n:
+        t0 = time.time()
+        oracle.solve(mech, T[:n2], P[:n2], Y[:n2], dt, n_threads=cores, **opts)
+        first = time.time() - t0
+        n = n2
+    return {"value": n / first, "unit": UNIT, "cores": min(cores, n), "kind": "oracle",
+            "sample": "first %d cells of the same workload, %.1f s" % (n, first)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle (plain C) on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    mech, T, P, Y, dt = workload(args.cells)
+    cores = os.cpu_count() or 1
+    opts = {} if args.max_iters is None else {"max_iters": args.max_iters}
+    per_step = max(cores, 8) * 2
+    off = 0
+    for _ in range(args.warmup):
+        oracle.solve(mech, T[off:off + per_step], P[off:off + per_step], Y[off:off + per_step],
+                     dt, n_threads=cores, **opts)
+        off += per_step
+    t0 = time.time()
+    for _ in range(args.steps):
+        oracle.solve(mech, T[off:off + per_step], P[off:off + per_step], Y[off:off + per_step],
+                     dt, n_threads=cores, **opts)
+        off += per_step
+    el = time.time() - t0
+    val = per_step * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "syn32x150, %d cells (oracle: %d-cell sample per step)"
+                       % (args.cells, per_step), "precision": "fp64"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d cells per step, %d steps" % (per_step, args.steps)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1905_09395_b300 import Mechanism, binding
+
+    rank, world, dist = dist_setup(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mech, T, P, Y, dt = workload(args.cells, rank)
+    S = mech.n_species
+    opts = dict(precision=binding.MIXED if args.precision == "mixed" else binding.FP64)
+    if args.max_iters is not None:
+        opts["max_iters"] = args.max_iters
+    m = Mechanism(mech, **opts)
+    n = len(T)
+    Td, Pd, Yd = (torch.from_numpy(a).to(dev) for a in (T, P, Y))
+    out = (torch.empty_like(Td), torch.empty_like(Yd), torch.empty(n, dtype=torch.int32, device=dev),
+           torch.empty(n, dtype=torch.uint8, device=dev))
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up: the same kernel and launch configuration on the first slice
+    nw = min(n, args.warmup_cells)
+    wout = tuple(x[:nw] for x in out)
+    for _ in range(args.warmup):
+        m.solve(Td[:nw], Pd[:nw], Yd[:nw], dt, out=wout)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.time()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            m.solve(Td, Pd, Yd, dt, out=out)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.time() - t0
+    barrier(dist)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(ms) / 1e3
+    iters = out[2].to(torch.int64)
+    cell_steps = int(iters.sum().item())
+    status = torch.bincount(out[3].to(torch.int64), minlength=4).cpu().numpy()
+    it_np = out[2].cpu().numpy()
+
+    # max over ranks
+    t_max = dev_s
+    total_cells = n * args.steps
+    if dist is not None:
+        t = torch.tensor([dev_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([float(total_cells)], device=dev)
+        dist.all_reduce(c)
+        total_cells = int(c.item())
+    value = total_cells / t_max
+
+    # end to end through the host-pointer entry point, pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        hT, hP, hY = pin(T), pin(P), pin(Y)
+        ho = (torch.empty(n, dtype=torch.float64).pin_memory().numpy(),
+              torch.empty((n, S), dtype=torch.float64).pin_memory().numpy(),
+              torch.empty(n, dtype=torch.int32).pin_memory().numpy(),
+              torch.empty(n, dtype=torch.uint8).pin_memory().numpy())
+        m.solve_host(hT[:nw], hP[:nw], hY[:nw], dt, out=tuple(x[:nw] for x in ho))
+        ke = max(1, args.e2e_steps)
+        barrier(dist)
+        t0 = time.time()
+        for _ in range(ke):
+            m.solve_host(hT, hP, hY, dt, out=ho)
+        el = time.time() - t0
+        if dist is not None:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": n * world * ke / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(hT.nbytes + hP.nbytes + hY.nbytes),
+               "d2h_bytes_per_step": int(sum(x.nbytes for x in ho)), "steps": ke}
+
+    if rank != 0:
+        return 0
+    ops = fp64_ops_per_cell_step(S, mech.n_reactions, int(mech.reversible.sum()),
+                                 len(mech.rxn_species))
+    per_launch_ops = ops * cell_steps
+    achieved = per_launch_ops / (float(np.mean(ms)) / 1e3)
+    roofline = {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * FP64_PEAK_OPS / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+                "pipe": "fp64 (DFMA = 2 flops; exp = %g, log = %g, div = %g DFMA-equivalents,"
+                        " measured)" % (EXP_OPS, LOG_OPS, DIV_OPS),
+                "ops_per_cell_step": ops, "cell_steps_per_launch": cell_steps,
+                "peak_source": "measured fp64 pipe rate, csrc/alu_peaks.cu"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "syn32x150 (32 species, 150 reversible reactions), %d cells, "
+                                   "T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), dt 1e-3 s"
+                                   % n,
+                       "precision": args.precision, "cells_per_gpu": n,
+                       "warmup_cells": nw, "max_iters": m.options.max_iters,
+                       "l2": "inputs (%d MB) larger than L2" % ((T.nbytes + P.nbytes + Y.nbytes)
+                                                                >> 20),
+                       "parallelism": "dp%d (independent cell batches)" % world},
+            "cell_steps_per_s": cell_steps * args.steps / t_max if world == 1 else None,
+            "iters": {"mean": float(it_np.mean()), "p50": float(np.percentile(it_np, 50)),
+                      "p99": float(np.percentile(it_np, 99)), "max": int(it_np.max())},
+            "cell_status": {"ok": int(status[0]), "maxiter": int(status[1]),
+                            "nonfinite": int(status[2]), "trange": int(status[3])},
+            "roofline": roofline, "gpu_launches": args.steps, "e2e": e2e,
+            "wall_s_timed": wall}
+    line["clocks"] = clk.summary()
+    if world == 1 and not args.no_cpu_baseline:
+        o = {} if args.max_iters is None else {"max_iters": args.max_iters}
+        line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **o)
+    print(json.dumps(line))
+    m.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--cells", type=int, default=N_CELLS)
+    ap.add_argument("--warmup-cells", type=int, default=16384)
+    ap.add_argument("--max-iters", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,147 @@
+/*
+ * stev.h - C ABI of the B300 STEV stiff-chemistry integrator.
+ *
+ * STEV (Buchheit et al., arXiv:1905.09395) integrates the chemical source
+ * terms of many independent CFD cells over one fluid time step t_f with
+ * forward Euler (Eq. 18), each cell on its own step size (Sec. 2.1, Eqs. 1-5),
+ * small-species damping of the rate laws (Sec. 2.2, Eqs. 6-7), a DFT ringing
+ * damper on reversible reactions (Sec. 2.3, Eqs. 8-14), and variable loading:
+ * a cell leaves the workload the iteration it reaches t_f (Sec. 2.4).
+ *
+ * Conventions for every entry point below:
+ *   - SI units: Pa, K, kg/mol, J/mol, mol/m^3, s.  Mass fractions Y.
+ *   - Cell arrays passed to stev_solve / stev_solve_soa are DEVICE pointers
+ *     owned by the caller; stev_solve_host takes HOST pointers.  Mechanism
+ *     tables passed to stev_mechanism_create are HOST pointers, copied.
+ *   - Calls are asynchronous on `cuda_stream` (NULL = legacy default stream)
+ *     unless stated otherwise; completion is observed through the stream.
+ *   - A mechanism owns its device tables and its per-slot solver state; at
+ *     most one solve may be in flight per mechanism at a time.
+ *   - Errors are returned as stev_status; stev_last_error() gives a message
+ *     (thread-local).  Per-cell outcomes go to the cell_status array.
+ */
+#ifndef STEV_H
+#define STEV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stev_mechanism stev_mechanism; /* opaque */
+
+typedef enum {
+  STEV_OK = 0,
+  STEV_EINVAL = 1,       /* bad argument or mechanism table */
+  STEV_ENOMEM = 2,       /* device or host allocation failed */
+  STEV_ECUDA = 3,        /* a CUDA call failed (message has the CUDA error) */
+  STEV_ETIMEOUT = 4,     /* a bounded wait gave up */
+  STEV_EUNBALANCED = 5,  /* a reaction does not conserve mass */
+  STEV_EINCOMPLETE = 6   /* the solver did not finish every cell */
+} stev_status;
+
+/* per-cell outcome written to cell_status[] */
+enum {
+  STEV_CELL_OK = 0,         /* reached t_f */
+  STEV_CELL_MAXITER = 1,    /* stopped at options.max_iters iterations */
+  STEV_CELL_NONFINITE = 2,  /* Y or T became NaN/Inf; state at that step */
+  STEV_CELL_TRANGE = 3      /* T left [200, 6000] K; state at that step */
+};
+
+enum { STEV_FP64 = 0, STEV_MIXED = 1 };            /* options.precision */
+enum { STEV_THERMO_POLY = 0, STEV_THERMO_MLP = 1 }; /* options.thermo */
+
+/* Solver parameters.  The paper names them but gives values for few; the
+ * defaults (stev_default_options) are the readings listed beside each. */
+typedef struct {
+  double y_step_max;  /* Y_step^max, Eq. 3: max mass-fraction consumption per step (1e-3) */
+  double delta_max;   /* delta^max, Eq. 4: h <= t_f * delta_max (0.01) */
+  double alpha;       /* Eq. 7 species limit factor; 0 disables (1e-5) */
+  int dft_n;          /* N, stored history length per reversible reaction, Sec. 2.3 (13) */
+  int dft_hi_first;   /* n, first high-frequency bin of Eq. 10 (4) */
+  double tol_ring;    /* Tol_ring, Eq. 12 (0.5) */
+  double tol_freq;    /* Tol_freq, Eq. 12, mol/m^3 (1e-6) */
+  double r_fac;       /* r_fac, Eq. 12, > 1 (2) */
+  double rof_min;     /* lower clamp keeping rOF > 0 (1e-30) */
+  int max_iters;      /* per-cell iteration cap (200000) */
+  int precision;      /* STEV_FP64 or STEV_MIXED */
+  int thermo;         /* STEV_THERMO_POLY or STEV_THERMO_MLP */
+  int dft_on;         /* 0 disables the Sec. 2.3 damper (1) */
+} stev_options;
+
+/* Fills *opt with the defaults above.  Never fails for a non-NULL opt. */
+void stev_default_options(stev_options *opt);
+
+/* Builds a mechanism from host tables and stages them on the current device.
+ *   n_species   S, 1..64;  n_reactions R, 1..512.
+ *   mol_weight  [S] kg/mol, > 0.
+ *   nasa7       [S][2][7] NASA-7 coefficients, low range then high range
+ *               (Sec. 3, Eqs. 15-16; a6 enthalpy and a7 entropy constants).
+ *   t_range     [S][3] T_low, T_split, T_high: T < T_split uses the low block.
+ *   rxn_ptr     [R+1] CSR row pointers into rxn_species / rxn_nu.
+ *   rxn_species [nnz] species index of each entry.
+ *   rxn_nu      [nnz] stoichiometric coefficient: < 0 reactant, > 0 product.
+ *               Reactions must be elementary: integer orders with at most two
+ *               molecules on each side (Sec. 4), each species at most once.
+ *   A, beta, Ea [R] Arrhenius k = A T^beta exp(-Ea/(R T)) (Eq. 29 form), SI.
+ *   reversible  [R] nonzero: reverse rate kf/K with K from Eq. 30.
+ *   opt         NULL for the defaults.
+ * Returns STEV_EINVAL for sizes out of range, non-finite or negative A,
+ * non-positive molar masses, bad indices or orders; STEV_EUNBALANCED when
+ * |sum nu W| > 1e-12 sum |nu W| for a reaction; STEV_ECUDA / STEV_ENOMEM on
+ * device failures.  On success *out owns the mechanism (free with
+ * stev_destroy).  Synchronous. */
+stev_status stev_mechanism_create(int n_species, int n_reactions, const double *mol_weight,
+                                  const double *nasa7, const double *t_range,
+                                  const int *rxn_ptr, const int *rxn_species,
+                                  const double *rxn_nu, const double *A, const double *beta,
+                                  const double *Ea, const unsigned char *reversible,
+                                  const stev_options *opt, stev_mechanism **out);
+
+/* Replaces the solver options of a mechanism (validated as in create). */
+stev_status stev_mechanism_set_options(stev_mechanism *mech, const stev_options *opt);
+
+/* Reads back the options in force. */
+stev_status stev_mechanism_get_options(const stev_mechanism *mech, stev_options *opt);
+
+/* Integrates n_cells independent cells over t_f = dt_cfd (Secs. 2.1-2.4).
+ *   T, P        [n_cells] initial temperature (K) and pressure (Pa), device.
+ *   Y           [n_cells][S] initial mass fractions (cell-major), device.
+ *   T_out, Y_out final state, same layouts; Y_out == Y and T_out == T are allowed.
+ *   iters       [n_cells] int32 iterations taken by each cell.
+ *   cell_status [n_cells] STEV_CELL_* per cell.
+ * n_cells == 0 is a no-op.  Returns STEV_EINVAL for NULL arrays with
+ * n_cells > 0, dt_cfd <= 0 or non-finite.  Asynchronous on cuda_stream. */
+stev_status stev_solve(stev_mechanism *mech, long n_cells, const double *T, const double *P,
+                       const double *Y, double dt_cfd, double *T_out, double *Y_out,
+                       int *iters, unsigned char *cell_status, void *cuda_stream);
+
+/* As stev_solve, but Y and Y_out are species-major [S][n_cells] (structure of
+ * arrays), the layout the solver works in; no transposes are made. */
+stev_status stev_solve_soa(stev_mechanism *mech, long n_cells, const double *T, const double *P,
+                           const double *Y_soa, double dt_cfd, double *T_out, double *Y_out_soa,
+                           int *iters, unsigned char *cell_status, void *cuda_stream);
+
+/* As stev_solve with HOST arrays: copies the inputs to the device, solves and
+ * copies the results back on cuda_stream, then waits for the stream.
+ * Device buffers are owned by the mechanism and reused across calls. */
+stev_status stev_solve_host(stev_mechanism *mech, long n_cells, const double *T, const double *P,
+                            const double *Y, double dt_cfd, double *T_out, double *Y_out,
+                            int *iters, unsigned char *cell_status, void *cuda_stream);
+
+/* Number of resident solver slots (cells in flight) of the persistent kernel
+ * on the current device for this mechanism and its options. */
+long stev_resident_slots(const stev_mechanism *mech);
+
+/* Frees a mechanism and everything it owns.  NULL is a no-op.  Waits for
+ * outstanding work of the mechanism to finish. */
+void stev_destroy(stev_mechanism *mech);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *stev_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STEV_H */

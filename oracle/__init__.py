@@ -60,23 +60,36 @@ class _Opts(ctypes.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
+# conditioning-probe builds: every kf scaled by one ulp (1 + 2^-52, 1 - 2^-53),
+# or every K by 64 ulp (1 +- 2^-46), the size of the rounding error of dG/RT
+PROBES = {"kf_up": ["-DORACLE_KF_SCALE=(1.0+2.220446049250313e-16)"],
+          "kf_down": ["-DORACLE_KF_SCALE=(1.0-1.1102230246251565e-16)"],
+          "K_up": ["-DORACLE_K_SCALE=(1.0+1.4210854715202004e-14)"],
+          "K_down": ["-DORACLE_K_SCALE=(1.0-1.4210854715202004e-14)"]}
+
+
+def _lib_path(probe: Optional[str]) -> str:
+    return _LIB if probe is None else os.path.join(_HERE, "liboracle_%s.so" % probe)
+
+
+def build(force: bool = False, probe: Optional[str] = None) -> str:
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
+    out = _lib_path(probe)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".%d.tmp" % os.getpid()
+        defs = [] if probe is None else PROBES[probe]
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               *defs, "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, out)
+    return out
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+def lib(probe: Optional[str] = None):
+    if probe not in _libs:
+        _lib = ctypes.CDLL(build(probe=probe))
         P = ctypes.c_void_p
         _lib.oracle_thermo.argtypes = [P, ctypes.c_double, P, P, P]
         _lib.oracle_rates.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P, P]
@@ -94,7 +107,8 @@ def lib():
         _lib.oracle_solve_cell_trace.restype = ctypes.c_int
         _lib.oracle_solve.argtypes = [P, P, ctypes.c_long, P, P, P, ctypes.c_double, P, P, P, P,
                                       ctypes.c_int]
-    return _lib
+        _libs[probe] = _lib
+    return _libs[probe]
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -202,8 +216,11 @@ def solve_cell_trace(mech, T0: float, P: float, Y0, dt: float, trace_cap: int = 
                 Y_trace=tY[:n])
 
 
-def solve(mech, T, P, Y, dt: float, n_threads: Optional[int] = None, **opts):
-    """All cells: returns (T_out, Y_out, iters, status)."""
+def solve(mech, T, P, Y, dt: float, n_threads: Optional[int] = None,
+          probe: Optional[str] = None, **opts):
+    """All cells: returns (T_out, Y_out, iters, status).
+
+    probe names one of the conditioning-probe builds in PROBES."""
     om = _om(mech)
     o = make_opts(**opts)
     T = np.ascontiguousarray(T, dtype=np.float64)
@@ -217,6 +234,24 @@ def solve(mech, T, P, Y, dt: float, n_threads: Optional[int] = None, **opts):
     if n_threads is None:
         n_threads = os.cpu_count() or 1
     n_threads = max(1, min(int(n_threads), n))
-    lib().oracle_solve(om.ref, ctypes.byref(o), n, _ptr(T), _ptr(P), _ptr(Y), float(dt), _ptr(To),
+    lib(probe).oracle_solve(om.ref, ctypes.byref(o), n, _ptr(T), _ptr(P), _ptr(Y), float(dt), _ptr(To),
                        _ptr(Yo), _ptr(iters), _ptr(status), n_threads)
     return To, Yo, iters, status
+
+
+def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] = None, **opts):
+    """Per-cell spread of the final state under rounding-size rate changes.
+
+    Returns (base_result, dY_spread[cells], dT_spread[cells]): the largest
+    |change| of Y (over species) and of T between the default build and the
+    probe builds (every kf off by one ulp, every K off by 64 ulp).  A cell whose spread is far below a tolerance is
+    well-conditioned at that tolerance."""
+    if base is None:
+        base = solve(mech, T, P, Y, dt, n_threads=n_threads, **opts)
+    dY = np.zeros(len(T))
+    dT = np.zeros(len(T))
+    for p in PROBES:
+        r = solve(mech, T, P, Y, dt, n_threads=n_threads, probe=p, **opts)
+        dY = np.maximum(dY, np.abs(r[1] - base[1]).max(axis=1))
+        dT = np.maximum(dT, np.abs(r[0] - base[0]))
+    return base, dY, dT

@@ -46,6 +46,18 @@
 #define ORACLE_PATM 101325.0       /* Pa, the 1 atm of Eq. 30 */
 #define ORACLE_PI 3.14159265358979323846
 
+/* Conditioning probe: the test suite also builds this file with kf scaled by
+ * 1 +- 1 ulp, or K scaled by 1 +- 64 ulp (the rounding error of dG/RT, a sum
+ * of terms up to ~64 in size, is of that order), to measure how far a cell's
+ * result moves under a rounding-size change of its rates.  The default build
+ * multiplies by exactly 1.0. */
+#ifndef ORACLE_KF_SCALE
+#define ORACLE_KF_SCALE 1.0
+#endif
+#ifndef ORACLE_K_SCALE
+#define ORACLE_K_SCALE 1.0
+#endif
+
 typedef struct {
   int n_species, n_reactions;
   const double *mol_weight;          /* [S] kg/mol */
@@ -130,7 +142,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
   /* Eqs. 29-30: kf = A T^beta exp(-Ea/RT);
    * K = (1 atm / RT)^dN exp(-dG/RT), dG/RT = sum nu (H/RT - S/R); kr = kf/K */
   for (int r = 0; r < R; ++r) {
-    double kf = m->A[r] * pow(T, m->beta[r]) * exp(-m->Ea[r] / (ORACLE_RU * T));
+    double kf = m->A[r] * pow(T, m->beta[r]) * exp(-m->Ea[r] / (ORACLE_RU * T)) * ORACLE_KF_SCALE;
     double fwd = kf, rev = 0.0;
     for (int k = m->rxn_ptr[r]; k < m->rxn_ptr[r + 1]; ++k) {
       double nu = m->rxn_nu[k];
@@ -143,7 +155,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
         dG += m->rxn_nu[k] * (hRT[s] - sR[s]);
         dN += m->rxn_nu[k];
       }
-      double K = pow(ORACLE_PATM / (ORACLE_RU * T), dN) * exp(-dG);
+      double K = pow(ORACLE_PATM / (ORACLE_RU * T), dN) * exp(-dG) * ORACLE_K_SCALE;
       double kr = kf / K;
       rev = kr;
       for (int k = m->rxn_ptr[r]; k < m->rxn_ptr[r + 1]; ++k) {

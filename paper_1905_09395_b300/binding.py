@@ -1,0 +1,208 @@
+"""ctypes binding of libstev.so (include/stev.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; this module
+checks shapes and dtypes, hands raw pointers over, and turns error codes into
+exceptions.  It never falls back to anything: without the built library every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstev.so")
+
+STEV_OK, STEV_EINVAL, STEV_ENOMEM, STEV_ECUDA, STEV_ETIMEOUT, STEV_EUNBALANCED, \
+    STEV_EINCOMPLETE = range(7)
+CELL_OK, CELL_MAXITER, CELL_NONFINITE, CELL_TRANGE = range(4)
+FP64, MIXED = 0, 1
+THERMO_POLY, THERMO_MLP = 0, 1
+
+# every symbol include/stev.h declares
+EXPORTS = (
+    "stev_default_options", "stev_mechanism_create", "stev_mechanism_set_options",
+    "stev_mechanism_get_options", "stev_solve", "stev_solve_soa", "stev_solve_host",
+    "stev_resident_slots", "stev_destroy", "stev_last_error",
+)
+
+
+class StevError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("stev error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("y_step_max", ctypes.c_double), ("delta_max", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("dft_n", ctypes.c_int), ("dft_hi_first", ctypes.c_int),
+        ("tol_ring", ctypes.c_double), ("tol_freq", ctypes.c_double),
+        ("r_fac", ctypes.c_double), ("rof_min", ctypes.c_double), ("max_iters", ctypes.c_int),
+        ("precision", ctypes.c_int), ("thermo", ctypes.c_int), ("dft_on", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libstev.so is not built (run __graft_entry__.build() or "
+                               "python paper_1905_09395_b300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, LNG = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+        L.stev_default_options.argtypes = [P]
+        L.stev_default_options.restype = None
+        L.stev_mechanism_create.argtypes = [I, I, P, P, P, P, P, P, P, P, P, P, P, P]
+        L.stev_mechanism_create.restype = I
+        L.stev_mechanism_set_options.argtypes = [P, P]
+        L.stev_mechanism_set_options.restype = I
+        L.stev_mechanism_get_options.argtypes = [P, P]
+        L.stev_mechanism_get_options.restype = I
+        for name in ("stev_solve", "stev_solve_soa", "stev_solve_host"):
+            f = getattr(L, name)
+            f.argtypes = [P, LNG, P, P, P, D, P, P, P, P, P]
+            f.restype = I
+        L.stev_resident_slots.argtypes = [P]
+        L.stev_resident_slots.restype = LNG
+        L.stev_destroy.argtypes = [P]
+        L.stev_destroy.restype = None
+        L.stev_last_error.argtypes = []
+        L.stev_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != STEV_OK:
+        raise StevError(code, lib().stev_last_error().decode())
+
+
+def default_options(**overrides) -> Options:
+    o = Options()
+    lib().stev_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Mechanism:
+    """A mechanism staged on the current CUDA device (stev_mechanism_create)."""
+
+    def __init__(self, tables, **options):
+        self._h = ctypes.c_void_p()
+        self.S = int(np.asarray(tables.mol_weight).shape[0])
+        self.R = int(np.asarray(tables.A).shape[0])
+        keep = dict(
+            W=_np(tables.mol_weight, np.float64), nasa7=_np(tables.nasa7, np.float64),
+            t_range=_np(tables.t_range, np.float64), ptr=_np(tables.rxn_ptr, np.int32),
+            sp=_np(tables.rxn_species, np.int32), nu=_np(tables.rxn_nu, np.float64),
+            A=_np(tables.A, np.float64), beta=_np(tables.beta, np.float64),
+            Ea=_np(tables.Ea, np.float64), rev=_np(tables.reversible, np.uint8))
+        opt = default_options(**options)
+        p = lambda a: a.ctypes.data
+        _check(lib().stev_mechanism_create(
+            self.S, self.R, p(keep["W"]), p(keep["nasa7"]), p(keep["t_range"]), p(keep["ptr"]),
+            p(keep["sp"]), p(keep["nu"]), p(keep["A"]), p(keep["beta"]), p(keep["Ea"]),
+            p(keep["rev"]), ctypes.byref(opt), ctypes.byref(self._h)))
+
+    # -- options ----------------------------------------------------------------
+    @property
+    def options(self) -> Options:
+        o = Options()
+        _check(lib().stev_mechanism_get_options(self._h, ctypes.byref(o)))
+        return o
+
+    def set_options(self, **changes):
+        o = self.options
+        for k, v in changes.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        _check(lib().stev_mechanism_set_options(self._h, ctypes.byref(o)))
+
+    @property
+    def resident_slots(self) -> int:
+        return int(lib().stev_resident_slots(self._h))
+
+    # -- device entry points ----------------------------------------------------
+    def _check_dev(self, T, P, Y, soa):
+        import torch
+        n = T.shape[0]
+        for name, t in (("T", T), ("P", P), ("Y", Y)):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+        if P.shape != (n,) or T.shape != (n,):
+            raise ValueError("T and P must have shape [n_cells]")
+        if Y.shape != ((self.S, n) if soa else (n, self.S)):
+            raise ValueError("Y has the wrong shape")
+        return n
+
+    def solve(self, T, P, Y, dt: float, out=None, stream=None, soa: bool = False):
+        """Device solve (stev_solve, or stev_solve_soa when soa=True).
+
+        T, P: [n] float64 CUDA tensors; Y: [n][S] (or [S][n] with soa=True).
+        Returns (T_out, Y_out, iters, status) CUDA tensors; asynchronous on
+        `stream` (default: torch's current stream)."""
+        import torch
+        n = self._check_dev(T, P, Y, soa)
+        if out is None:
+            out = (torch.empty_like(T), torch.empty_like(Y),
+                   torch.empty(n, dtype=torch.int32, device=T.device),
+                   torch.empty(n, dtype=torch.uint8, device=T.device))
+        To, Yo, it, st = out
+        fn = lib().stev_solve_soa if soa else lib().stev_solve
+        _check(fn(self._h, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(), float(dt), To.data_ptr(),
+                  Yo.data_ptr(), it.data_ptr(), st.data_ptr(), _stream_handle(stream)))
+        return To, Yo, it, st
+
+    def solve_host(self, T, P, Y, dt: float, out=None, stream=None):
+        """Host-pointer solve (stev_solve_host): numpy in, numpy out, blocking."""
+        T, P, Y = _np(T, np.float64), _np(P, np.float64), _np(Y, np.float64)
+        n = T.shape[0]
+        if P.shape != (n,) or Y.shape != (n, self.S):
+            raise ValueError("bad shapes")
+        if out is None:
+            out = (np.empty(n), np.empty((n, self.S)), np.empty(n, np.int32), np.empty(n, np.uint8))
+        To, Yo, it, st = out
+        h = 0 if stream is None else _stream_handle(stream)
+        _check(lib().stev_solve_host(self._h, n, T.ctypes.data, P.ctypes.data, Y.ctypes.data,
+                                     float(dt), To.ctypes.data, Yo.ctypes.data, it.ctypes.data,
+                                     st.ctypes.data, h))
+        return To, Yo, it, st
+
+    def close(self):
+        if self._h:
+            lib().stev_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,445 @@
+// C ABI of the STEV integrator: mechanism staging, launch configuration and
+// the solve entry points declared in include/stev.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/stev.h"
+#include "stev_device.cuh"
+#include "stev_fp64.cuh"
+
+using namespace stev;
+
+// ----------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+static stev_status fail(stev_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? STEV_ENOMEM : STEV_ECUDA,            \
+                  "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+// -------------------------------------------------------------- mechanism
+struct stev_mechanism {
+  int device = 0;
+  int S = 0, R = 0, Rrev = 0, n_gather = 0;
+  stev_options opt{};
+  int n_hi_bins = 0;
+  double* d_sp = nullptr;
+  double* d_rx = nullptr;
+  int4* d_ri = nullptr;
+  int* d_gptr = nullptr;
+  int* d_gent = nullptr;
+  double* d_tw = nullptr;
+  // launch configuration of the persistent kernel
+  int G = 32;              // lanes per cell
+  int block = 0, grid = 0; // threads per CTA, CTAs
+  size_t smem = 0;
+  long long nslots = 0;    // cells resident at once
+  unsigned long long* d_counter = nullptr;
+  // device copies for the host-pointer entry point
+  double *d_hT = nullptr, *d_hP = nullptr, *d_hY = nullptr, *d_hTo = nullptr, *d_hYo = nullptr;
+  int* d_hit = nullptr;
+  unsigned char* d_hst = nullptr;
+  long long host_cap = 0;
+};
+
+extern "C" void stev_default_options(stev_options* o) {
+  if (!o) return;
+  o->y_step_max = 1e-3;
+  o->delta_max = 0.01;
+  o->alpha = 1e-5;
+  o->dft_n = 13;
+  o->dft_hi_first = 4;
+  o->tol_ring = 0.5;
+  o->tol_freq = 1e-6;
+  o->r_fac = 2.0;
+  o->rof_min = 1e-30;
+  o->max_iters = 200000;
+  o->precision = STEV_FP64;
+  o->thermo = STEV_THERMO_POLY;
+  o->dft_on = 1;
+}
+
+static stev_status check_options(const stev_options* o) {
+  if (!(o->y_step_max > 0.0) || !std::isfinite(o->y_step_max))
+    return fail(STEV_EINVAL, "y_step_max must be finite and > 0");
+  if (!(o->delta_max > 0.0 && o->delta_max <= 1.0)) return fail(STEV_EINVAL, "delta_max must be in (0, 1]");
+  if (!(o->alpha >= 0.0) || !std::isfinite(o->alpha)) return fail(STEV_EINVAL, "alpha must be finite and >= 0");
+  if (o->dft_n < 2 || o->dft_n > kMaxDftN) return fail(STEV_EINVAL, "dft_n must be in [2, %d]", kMaxDftN);
+  if (o->dft_hi_first < 1 || o->dft_hi_first > o->dft_n / 2)
+    return fail(STEV_EINVAL, "dft_hi_first must be in [1, dft_n/2]");
+  if (!(o->r_fac > 0.0) || !std::isfinite(o->r_fac)) return fail(STEV_EINVAL, "r_fac must be finite and > 0");
+  if (!std::isfinite(o->tol_ring) || !std::isfinite(o->tol_freq)) return fail(STEV_EINVAL, "tolerances must be finite");
+  if (!(o->rof_min > 0.0 && o->rof_min <= 1.0)) return fail(STEV_EINVAL, "rof_min must be in (0, 1]");
+  if (o->max_iters < 1) return fail(STEV_EINVAL, "max_iters must be >= 1");
+  if (o->precision != STEV_FP64 && o->precision != STEV_MIXED) return fail(STEV_EINVAL, "unknown precision");
+  if (o->thermo != STEV_THERMO_POLY && o->thermo != STEV_THERMO_MLP) return fail(STEV_EINVAL, "unknown thermo mode");
+  if (o->precision == STEV_MIXED || o->thermo == STEV_THERMO_MLP)
+    return fail(STEV_EINVAL, "precision/thermo mode not available in this build");
+  return STEV_OK;
+}
+
+static void free_mech(stev_mechanism* m) {
+  void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_counter,
+                  m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete m;
+}
+
+typedef void (*KernelFn)(Launch);
+
+static KernelFn fp64_kernel(int G) {
+  switch (G) {
+    case 8: return stev_fp64_kernel<8>;
+    case 16: return stev_fp64_kernel<16>;
+    default: return stev_fp64_kernel<32>;
+  }
+}
+
+// Lanes per cell: enough to cover the species and most reactions in one or
+// two rounds without leaving most lanes idle on small mechanisms.
+static int choose_group(int S, int R) {
+  if (S <= 8 && R <= 32) return 8;
+  if (S <= 16 && R <= 64) return 16;
+  return 32;
+}
+
+// Launch configuration of the persistent kernel: as many resident cells per
+// CTA as shared memory holds (whole warps, <= kMaxBlock threads), then as
+// many CTAs as fit on every SM.
+static stev_status configure(stev_mechanism* m) {
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, m->device));
+  m->G = choose_group(m->S, m->R);
+  const int G = m->G;
+  const size_t tables = table_smem_bytes(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n);
+  const size_t cell = cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
+  const size_t limit = prop.sharedMemPerBlockOptin;
+  if (tables + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
+  int cells = (int)((limit - tables) / cell);
+  cells = std::min(cells, kMaxBlock / G);
+  const int per_warp = 32 / G;
+  cells = (cells / per_warp) * per_warp;
+  if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
+  const size_t smem = tables + (size_t)cells * cell;
+  KernelFn k = fp64_kernel(G);
+  CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cells * G, smem));
+  if (per_sm < 1) return fail(STEV_EINVAL, "persistent kernel cannot be resident");
+  m->block = cells * G;
+  m->grid = per_sm * prop.multiProcessorCount;
+  m->smem = smem;
+  m->nslots = (long long)m->grid * cells;
+  if (!m->d_counter) CUDA_TRY(cudaMalloc(&m->d_counter, sizeof(unsigned long long)));
+  return STEV_OK;
+}
+
+extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, const double* nasa7,
+                                             const double* t_range, const int* rxn_ptr,
+                                             const int* rxn_species, const double* rxn_nu,
+                                             const double* A, const double* beta, const double* Ea,
+                                             const unsigned char* reversible,
+                                             const stev_options* opt, stev_mechanism** out) {
+  g_err.clear();
+  if (!out) return fail(STEV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (S < 1 || S > kMaxSpecies) return fail(STEV_EINVAL, "n_species must be in [1, %d]", kMaxSpecies);
+  if (R < 1 || R > kMaxReactions) return fail(STEV_EINVAL, "n_reactions must be in [1, %d]", kMaxReactions);
+  if (!W || !nasa7 || !t_range || !rxn_ptr || !rxn_species || !rxn_nu || !A || !beta || !Ea || !reversible)
+    return fail(STEV_EINVAL, "NULL table pointer");
+  stev_options o;
+  if (opt) o = *opt; else stev_default_options(&o);
+  stev_status st = check_options(&o);
+  if (st != STEV_OK) return st;
+
+  // species tables
+  std::vector<double> sp((size_t)S * SP_STRIDE, 0.0);
+  for (int i = 0; i < S; ++i) {
+    if (!(W[i] > 0.0) || !std::isfinite(W[i])) return fail(STEV_EINVAL, "mol_weight[%d] must be finite and > 0", i);
+    double* e = &sp[(size_t)i * SP_STRIDE];
+    e[SP_W] = W[i];
+    e[SP_INVW] = 1.0 / W[i];
+    e[SP_TSPLIT] = t_range[3 * i + 1];
+    if (!std::isfinite(e[SP_TSPLIT])) return fail(STEV_EINVAL, "t_range[%d] not finite", i);
+    for (int rg = 0; rg < 2; ++rg) {
+      const double* a = nasa7 + ((size_t)i * 2 + rg) * 7;
+      for (int k = 0; k < 7; ++k)
+        if (!std::isfinite(a[k])) return fail(STEV_EINVAL, "nasa7[%d][%d][%d] not finite", i, rg, k);
+      double* b = e + (rg == 0 ? SP_LOW : SP_HIGH);
+      for (int k = 0; k < 7; ++k) b[B_A0 + k] = a[k];
+      b[B_H1] = a[1] / 2.0;
+      b[B_H2] = a[2] / 3.0;
+      b[B_H3] = a[3] / 4.0;
+      b[B_H4] = a[4] / 5.0;
+      b[B_G2] = a[2] / 6.0;
+      b[B_G3] = a[3] / 12.0;
+      b[B_G4] = a[4] / 20.0;
+    }
+  }
+
+  // reaction tables
+  if (rxn_ptr[0] != 0) return fail(STEV_EINVAL, "rxn_ptr[0] must be 0");
+  std::vector<double> rx((size_t)R * RX_STRIDE, 0.0);
+  std::vector<int4> ri(R);
+  int nrev = 0;
+  for (int r = 0; r < R; ++r) {
+    const int lo = rxn_ptr[r], hi = rxn_ptr[r + 1];
+    if (hi <= lo || hi - lo > 4) return fail(STEV_EINVAL, "reaction %d: bad rxn_ptr range", r);
+    int reac[2], prod[2], nr = 0, np = 0;
+    double bal = 0.0, mag = 0.0;
+    for (int k = lo; k < hi; ++k) {
+      const int s = rxn_species[k];
+      const double nu = rxn_nu[k];
+      if (s < 0 || s >= S) return fail(STEV_EINVAL, "reaction %d: species index %d out of range", r, s);
+      for (int k2 = lo; k2 < k; ++k2)
+        if (rxn_species[k2] == s) return fail(STEV_EINVAL, "reaction %d: species %d listed twice", r, s);
+      if (!(nu == -2.0 || nu == -1.0 || nu == 1.0 || nu == 2.0))
+        return fail(STEV_EINVAL, "reaction %d: only elementary orders |nu| in {1,2} are supported", r);
+      const int mult = (int)std::fabs(nu);
+      for (int t = 0; t < mult; ++t) {
+        if (nu < 0) { if (nr == 2) return fail(STEV_EINVAL, "reaction %d: more than two reactant molecules", r); reac[nr++] = s; }
+        else        { if (np == 2) return fail(STEV_EINVAL, "reaction %d: more than two product molecules", r); prod[np++] = s; }
+      }
+      bal += nu * W[s];
+      mag += std::fabs(nu * W[s]);
+    }
+    if (nr == 0 || np == 0) return fail(STEV_EINVAL, "reaction %d needs reactants and products", r);
+    if (std::fabs(bal) > 1e-12 * mag) return fail(STEV_EUNBALANCED, "reaction %d is not mass-balanced", r);
+    if (!(A[r] >= 0.0) || !std::isfinite(A[r])) return fail(STEV_EINVAL, "A[%d] must be finite and >= 0", r);
+    if (!std::isfinite(beta[r]) || !std::isfinite(Ea[r])) return fail(STEV_EINVAL, "beta/Ea[%d] not finite", r);
+    double* e = &rx[(size_t)r * RX_STRIDE];
+    e[RX_LNA] = std::log(A[r]);
+    e[RX_BETA] = beta[r];
+    e[RX_EAR] = Ea[r] / kRu;
+    const int a0 = reac[0], a1 = nr > 1 ? reac[1] : kNone;
+    const int p0 = prod[0], p1 = np > 1 ? prod[1] : kNone;
+    ri[r].x = a0 | (a1 << 8) | (p0 << 16) | (p1 << 24);
+    ri[r].y = np - nr;
+    ri[r].z = reversible[r] ? 1 : 0;
+    ri[r].w = reversible[r] ? nrev++ : -1;
+  }
+
+  // species-major gather lists in ascending reaction order
+  std::vector<int> gptr(S + 1, 0), gent;
+  for (int i = 0; i < S; ++i) {
+    for (int r = 0; r < R; ++r)
+      for (int k = rxn_ptr[r]; k < rxn_ptr[r + 1]; ++k)
+        if (rxn_species[k] == i) gent.push_back(gather_pack(r, (int)rxn_nu[k]));
+    gptr[i + 1] = (int)gent.size();
+  }
+
+  stev_mechanism* m = new stev_mechanism();
+  m->S = S;
+  m->R = R;
+  m->Rrev = nrev;
+  m->n_gather = (int)gent.size();
+  m->opt = o;
+  if (cudaGetDevice(&m->device) != cudaSuccess) { delete m; return fail(STEV_ECUDA, "no CUDA device"); }
+  m->n_hi_bins = o.dft_n / 2 - o.dft_hi_first + 1;
+  std::vector<double> tw((size_t)m->n_hi_bins * 2 * o.dft_n);
+  for (int b = 0; b < m->n_hi_bins; ++b) {
+    const int j = o.dft_hi_first + b;
+    for (int k = 0; k < o.dft_n; ++k) {
+      const double ang = -2.0 * M_PI * (double)j * (double)k / (double)o.dft_n;
+      tw[(size_t)b * 2 * o.dft_n + k] = std::cos(ang);
+      tw[(size_t)b * 2 * o.dft_n + o.dft_n + k] = std::sin(ang);
+    }
+  }
+#define TRY_OR_FREE(expr)            \
+  do {                               \
+    stev_status s_ = (expr);         \
+    if (s_ != STEV_OK) {             \
+      free_mech(m);                  \
+      return s_;                     \
+    }                                \
+  } while (0)
+  auto upload = [&](void** dst, const void* src, size_t bytes) -> stev_status {
+    CUDA_TRY(cudaMalloc(dst, bytes ? bytes : 16));
+    if (bytes) CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return STEV_OK;
+  };
+  TRY_OR_FREE(upload((void**)&m->d_sp, sp.data(), sp.size() * sizeof(double)));
+  TRY_OR_FREE(upload((void**)&m->d_rx, rx.data(), rx.size() * sizeof(double)));
+  TRY_OR_FREE(upload((void**)&m->d_ri, ri.data(), ri.size() * sizeof(int4)));
+  TRY_OR_FREE(upload((void**)&m->d_tw, tw.data(), tw.size() * sizeof(double)));
+  TRY_OR_FREE(upload((void**)&m->d_gptr, gptr.data(), gptr.size() * sizeof(int)));
+  TRY_OR_FREE(upload((void**)&m->d_gent, gent.data(), gent.size() * sizeof(int)));
+  TRY_OR_FREE(configure(m));
+  *out = m;
+  return STEV_OK;
+}
+
+extern "C" stev_status stev_mechanism_set_options(stev_mechanism* m, const stev_options* opt) {
+  g_err.clear();
+  if (!m || !opt) return fail(STEV_EINVAL, "NULL argument");
+  stev_status st = check_options(opt);
+  if (st != STEV_OK) return st;
+  if (opt->dft_n != m->opt.dft_n || opt->dft_hi_first != m->opt.dft_hi_first) {
+    // the twiddle table depends on N and n
+    const int nb = opt->dft_n / 2 - opt->dft_hi_first + 1;
+    std::vector<double> tw((size_t)nb * 2 * opt->dft_n);
+    for (int b = 0; b < nb; ++b) {
+      const int j = opt->dft_hi_first + b;
+      for (int k = 0; k < opt->dft_n; ++k) {
+        const double ang = -2.0 * M_PI * (double)j * (double)k / (double)opt->dft_n;
+        tw[(size_t)b * 2 * opt->dft_n + k] = std::cos(ang);
+        tw[(size_t)b * 2 * opt->dft_n + opt->dft_n + k] = std::sin(ang);
+      }
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (m->d_tw) cudaFree(m->d_tw);
+    m->d_tw = nullptr;
+    CUDA_TRY(cudaMalloc(&m->d_tw, tw.size() * sizeof(double)));
+    CUDA_TRY(cudaMemcpy(m->d_tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    m->n_hi_bins = nb;
+  }
+  m->opt = *opt;
+  return configure(m);
+}
+
+extern "C" stev_status stev_mechanism_get_options(const stev_mechanism* m, stev_options* opt) {
+  if (!m || !opt) return fail(STEV_EINVAL, "NULL argument");
+  *opt = m->opt;
+  return STEV_OK;
+}
+
+extern "C" long stev_resident_slots(const stev_mechanism* m) { return m ? (long)m->nslots : 0; }
+
+static Launch make_launch(stev_mechanism* m, long long n, double dt) {
+  Launch L{};
+  L.S = m->S;
+  L.R = m->R;
+  L.Rrev = m->Rrev;
+  L.n_gather = m->n_gather;
+  L.sp_tab = m->d_sp;
+  L.rx_tab = m->d_rx;
+  L.rx_idx = m->d_ri;
+  L.g_ptr = m->d_gptr;
+  L.g_ent = m->d_gent;
+  L.dft_tw = m->d_tw;
+  L.n_hi_bins = m->n_hi_bins;
+  L.dft_n = m->opt.dft_n;
+  L.dft_on = m->opt.dft_on;
+  L.max_iters = m->opt.max_iters;
+  L.y_step_max = m->opt.y_step_max;
+  L.delta_max = m->opt.delta_max;
+  L.alpha = m->opt.alpha;
+  L.tol_ring = m->opt.tol_ring;
+  L.tol_freq = m->opt.tol_freq;
+  L.r_fac = m->opt.r_fac;
+  L.rof_min = m->opt.rof_min;
+  L.ln_patm_over_ru = std::log(kPatm / kRu);
+  L.n_cells = n;
+  L.dt = dt;
+  L.counter = m->d_counter;
+  return L;
+}
+
+static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, const void* P,
+                                    const void* Y, double dt, const void* To, const void* Yo,
+                                    const void* it, const void* cs) {
+  if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (n < 0) return fail(STEV_EINVAL, "n_cells < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(STEV_EINVAL, "dt_cfd must be finite and > 0");
+  if (n > 0 && (!T || !P || !Y || !To || !Yo || !it || !cs)) return fail(STEV_EINVAL, "NULL array");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(STEV_EINVAL, "mechanism lives on device %d, current is %d", m->device, dev);
+  return STEV_OK;
+}
+
+static stev_status launch_persistent(stev_mechanism* m, const Launch& L, cudaStream_t s) {
+  CUDA_TRY(cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned long long), s));
+  fp64_kernel(m->G)<<<m->grid, m->block, m->smem, s>>>(L);
+  CUDA_TRY(cudaGetLastError());
+  return STEV_OK;
+}
+
+static stev_status solve_impl(stev_mechanism* m, long n, const double* T, const double* P,
+                              const double* Y, double dt, double* T_out, double* Y_out,
+                              int* iters, unsigned char* cell_status, void* stream, int soa) {
+  g_err.clear();
+  stev_status st = check_solve_args(m, n, T, P, Y, dt, T_out, Y_out, iters, cell_status);
+  if (st != STEV_OK || n == 0) return st;
+  Launch L = make_launch(m, n, dt);
+  L.T = T; L.P = P; L.Y = Y;
+  L.T_out = T_out; L.Y_out = Y_out; L.iters = iters; L.status = cell_status;
+  L.y_soa = soa;
+  return launch_persistent(m, L, (cudaStream_t)stream);
+}
+
+extern "C" stev_status stev_solve(stev_mechanism* m, long n, const double* T, const double* P,
+                                  const double* Y, double dt, double* T_out, double* Y_out,
+                                  int* iters, unsigned char* cell_status, void* stream) {
+  return solve_impl(m, n, T, P, Y, dt, T_out, Y_out, iters, cell_status, stream, 0);
+}
+
+extern "C" stev_status stev_solve_soa(stev_mechanism* m, long n, const double* T, const double* P,
+                                      const double* Y, double dt, double* T_out, double* Y_out,
+                                      int* iters, unsigned char* cell_status, void* stream) {
+  return solve_impl(m, n, T, P, Y, dt, T_out, Y_out, iters, cell_status, stream, 1);
+}
+
+extern "C" stev_status stev_solve_host(stev_mechanism* m, long n, const double* T, const double* P,
+                                       const double* Y, double dt, double* T_out, double* Y_out,
+                                       int* iters, unsigned char* cell_status, void* stream) {
+  g_err.clear();
+  if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (n < 0) return fail(STEV_EINVAL, "n_cells < 0");
+  if (n == 0) return STEV_OK;
+  if (!T || !P || !Y || !T_out || !Y_out || !iters || !cell_status) return fail(STEV_EINVAL, "NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > m->host_cap) {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    void** bufs[] = {(void**)&m->d_hT, (void**)&m->d_hP, (void**)&m->d_hY, (void**)&m->d_hTo,
+                     (void**)&m->d_hYo, (void**)&m->d_hit, (void**)&m->d_hst};
+    for (void** b : bufs) { if (*b) cudaFree(*b); *b = nullptr; }
+    m->host_cap = 0;
+    const size_t sz[] = {(size_t)n * 8, (size_t)n * 8, (size_t)n * m->S * 8, (size_t)n * 8,
+                         (size_t)n * m->S * 8, (size_t)n * 4, (size_t)n};
+    for (int k = 0; k < 7; ++k) CUDA_TRY(cudaMalloc(bufs[k], sz[k]));
+    m->host_cap = n;
+  }
+  CUDA_TRY(cudaMemcpyAsync(m->d_hT, T, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(m->d_hP, P, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(m->d_hY, Y, (size_t)n * m->S * 8, cudaMemcpyHostToDevice, s));
+  stev_status st = stev_solve(m, n, m->d_hT, m->d_hP, m->d_hY, dt, m->d_hTo, m->d_hYo, m->d_hit,
+                              m->d_hst, stream);
+  if (st != STEV_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(T_out, m->d_hTo, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(Y_out, m->d_hYo, (size_t)n * m->S * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(iters, m->d_hit, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(cell_status, m->d_hst, (size_t)n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return STEV_OK;
+}
+
+extern "C" void stev_destroy(stev_mechanism* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  free_mech(m);
+}
+
+extern "C" const char* stev_last_error(void) { return g_err.c_str(); }

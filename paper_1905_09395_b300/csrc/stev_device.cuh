@@ -1,0 +1,85 @@
+// Device-side data layout shared by the STEV kernels (not by the oracle).
+//
+// Mechanism tables are built once on the host (stev_capi.cu) and staged into
+// shared memory by every CTA of the persistent kernel:
+//   species  : SP_STRIDE doubles each: W, 1/W, T_split, pad, low block, high block
+//   block    : a0..a6 of NASA-7 plus pre-divided coefficients so that
+//              cp/R = a0 + T(a1 + T(a2 + T(a3 + T a4)))                (Eq. 15)
+//              H/RT = a0 + T(a1/2 + T(a2/3 + T(a3/4 + T a4/5))) + a5/T (Eq. 16)
+//              G/RT = H/RT - S/R
+//                   = a0(1 - lnT) - T(a1/2 + T(a2/6 + T(a3/12 + T a4/20))) + a5/T - a6
+//   reaction : lnA, beta, Ea/R (Eq. 29 in log form) and an int4 with the
+//              packed species slots (two reactant, two product, 0xFF = none;
+//              a species of order 2 fills both slots), dN = sum(nu), the
+//              reversible flag and the reaction's index among reversible ones.
+//   gather   : species-major lists of (reaction, nu) in ascending reaction
+//              order, so that wdot_i = sum_r nu_ir q_r is summed in the same
+//              order as a reaction-major scatter would add into it.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace stev {
+
+constexpr int kMaxSpecies = 64;
+constexpr int kMaxReactions = 512;
+constexpr int kMaxDftN = 32;
+constexpr int kMaxGatherEntries = 4 * kMaxReactions;
+constexpr double kRu = 8.314462618;     // J/(mol K)
+constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
+constexpr int kNone = 0xFF;
+constexpr int kMaxBlock = 512;       // threads per CTA of the persistent kernels
+
+enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
+enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
+       B_SIZE };
+enum { RX_LNA = 0, RX_BETA = 1, RX_EAR = 2, RX_STRIDE = 4 };
+
+// gather entry: reaction index * 16 + (nu + 8)
+__host__ __device__ inline int gather_pack(int r, int nu) { return r * 16 + (nu + 8); }
+
+// Everything a launch needs, passed by value.
+struct Launch {
+  // mechanism
+  int S, R, Rrev, n_gather;
+  const double* sp_tab;   // [S][SP_STRIDE]
+  const double* rx_tab;   // [R][RX_STRIDE]
+  const int4* rx_idx;     // [R]
+  const int* g_ptr;       // [S+1] species-major gather lists
+  const int* g_ent;       // [n_gather]
+  const double* dft_tw;   // [n_hi_bins][2][dft_n]: cos, sin of -2 pi j m / N
+  int n_hi_bins;
+  // options (Secs. 2.1-2.3)
+  int dft_n, dft_on, max_iters;
+  double y_step_max, delta_max, alpha, tol_ring, tol_freq, r_fac, rof_min;
+  double ln_patm_over_ru;  // ln(P_atm / R_u)
+  // work
+  long long n_cells;
+  double dt;
+  const double* T;        // [n]
+  const double* P;        // [n]
+  const double* Y;        // [n][S] if !y_soa else [S][n]
+  double* T_out;          // [n]
+  double* Y_out;          // same layout as Y
+  int* iters;             // [n]
+  unsigned char* status;  // [n]
+  int y_soa;
+  unsigned long long* counter;  // next unclaimed cell
+};
+
+// Shared-memory footprint of the tables (bytes, 16-byte aligned).
+__host__ __device__ inline size_t table_smem_bytes(int S, int R, int n_gather, int n_hi_bins,
+                                                   int dft_n) {
+  size_t b = (size_t)S * SP_STRIDE * 8 + (size_t)R * RX_STRIDE * 8 + (size_t)R * 16 +
+             (size_t)n_hi_bins * 2 * dft_n * 8 + (size_t)(S + 1 + n_gather) * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+// Shared-memory footprint of one resident cell in the FP64 kernel: Y, C, G/RT,
+// H/RT (S each), effective rates (R), history [N][Rrev] and rOF (Rrev).
+__host__ __device__ inline size_t cell_smem_bytes_fp64(int S, int R, int Rrev, int dft_n) {
+  size_t b = ((size_t)4 * S + R + (size_t)dft_n * Rrev + Rrev) * 8;
+  return (b + 15) & ~(size_t)15;
+}
+
+}  // namespace stev

@@ -1,0 +1,310 @@
+// Plain FP64 STEV: the persistent, compacting step kernel.
+//
+// A group of G lanes (G = 8, 16 or 32, chosen per mechanism) integrates one
+// cell at a time.  Lanes split the species (i = lane, lane+G, ...) and the
+// reactions (r = lane, lane+G, ...) of their cell.  Every piece of a resident
+// cell's state lives in shared memory: Y, the gamma-stabilised
+// concentrations, G/RT, H/RT, the effective rates of progress, the N-value
+// ringing history of every reversible reaction (Eq. 8) and rOF (Eqs. 11-13),
+// so a step touches global memory only to read the mechanism once per CTA and
+// to load/store whole cells.  Group-wide sums and the limiter's minimum are
+// xor-butterfly shuffles, which leave bit-identical results in every lane.
+//
+// Production rates are gathered species-major: lane i sums nu_ir q_r over
+// the reactions of species i in ascending r, the order of the oracle's
+// reaction-major scatter, with no atomics.
+//
+// Variable load (Sec. 2.4): a group whose cell reaches t_f writes it out and
+// takes the next cell.  The warp gathers the groups that need work with
+// __ballot_sync (one bit per group leader), claims that many consecutive cell
+// ids with a single atomicAdd and hands them out by the popcount of the lower
+// groups.  Groups left without work once the queue is empty keep stepping a
+// dead state (no memory writes) so that the warp's shuffles stay convergent;
+// the warp exits when none of its groups holds a cell.  The kernel has no
+// waits: every loop is bounded by the mechanism size or max_iters.
+#pragma once
+#include "stev_device.cuh"
+
+namespace stev {
+
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// Minimum of num/den over the group (den > 0; den == 0 encodes +inf), with a
+// symmetric tie-break so that every lane keeps the same pair.
+template <int G>
+__device__ __forceinline__ void group_min_frac(double& num, double& den) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const double n2 = __shfl_xor_sync(0xffffffffu, num, o, G);
+    const double d2 = __shfl_xor_sync(0xffffffffu, den, o, G);
+    const double a = n2 * den, b = num * d2;
+    const bool take = (a < b) || (a == b && (n2 < num || (n2 == num && d2 < den)));
+    if (take) { num = n2; den = d2; }
+  }
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool v) {
+  const unsigned b = __ballot_sync(0xffffffffu, v);
+  const int base = (threadIdx.x & 31) & ~(G - 1);
+  const unsigned m = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+  return (b & m) != 0u;
+}
+
+struct CellState {
+  long long cell;   // -1 when the group has no cell
+  double T, P, t_rem;
+  int it;
+  int nhist;
+};
+
+struct Tables {
+  const double* sp;
+  const double* rx;
+  const int4* ri;
+  const int* gptr;
+  const int* gent;
+  const double* tw;
+};
+
+// One STEV iteration of one cell by its group (Secs. 2.1-2.3, Eq. 18).
+// Returns -1 to continue, else the STEV_CELL_* outcome.
+template <int G>
+__device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, double* cY, double* cC,
+                                         double* cG, double* cH, double* cQ, double* cHist,
+                                         double* cRof, int l, CellState& st) {
+  const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
+  const double T = st.T;
+  const double lnT = log(T);
+  const double invT = 1.0 / T;
+
+  // mixture: sum Y/W and ideal-gas density
+  double part = 0.0;
+  for (int i = l; i < S; i += G) part = fma(cY[i], tb.sp[i * SP_STRIDE + SP_INVW], part);
+  const double sumYW = group_sum<G>(part);
+  const double rho = st.P / (kRu * T * sumYW);
+
+  // thermo (Eqs. 15-16, G/RT) and gamma-stabilised concentrations (Eqs. 6-7)
+  double cpp = 0.0;
+  for (int i = l; i < S; i += G) {
+    const double* sp = tb.sp + i * SP_STRIDE;
+    const double* b = sp + (T < sp[SP_TSPLIT] ? SP_LOW : SP_HIGH);
+    const double Yi = cY[i];
+    const double cpR = fma(fma(fma(fma(b[B_A4], T, b[B_A3]), T, b[B_A2]), T, b[B_A1]), T, b[B_A0]);
+    const double hp = fma(fma(fma(b[B_H4], T, b[B_H3]), T, b[B_H2]), T, b[B_H1]);
+    cH[i] = fma(hp, T, b[B_A0]) + b[B_A5] * invT;
+    const double gp = fma(fma(fma(b[B_G4], T, b[B_G3]), T, b[B_G2]), T, b[B_H1]);
+    cG[i] = fma(b[B_A0], 1.0 - lnT, fma(b[B_A5], invT, -b[B_A6])) - gp * T;
+    cpp = fma(Yi * cpR, sp[SP_INVW], cpp);
+    const double y = fmax(Yi, 0.0);
+    const double ys = (L.alpha > 0.0) ? y * (y / (L.alpha + y)) : y;
+    cC[i] = rho * ys * sp[SP_INVW];
+  }
+  const double cpsum = group_sum<G>(cpp);
+  __syncwarp();
+
+  // rates of progress (Eqs. 29-30 in log form) and effective rates (Eq. 14)
+  const double lnPref = L.ln_patm_over_ru - lnT;  // ln(P_atm / (R T))
+  const int ktap = st.nhist % N;
+  for (int r = l; r < R; r += G) {
+    const double* rx = tb.rx + r * RX_STRIDE;
+    const int4 ri = tb.ri[r];
+    const int a0 = ri.x & 0xFF, a1 = (ri.x >> 8) & 0xFF;
+    const int p0 = (ri.x >> 16) & 0xFF, p1 = (ri.x >> 24) & 0xFF;
+    const double lnkf = fma(rx[RX_BETA], lnT, rx[RX_LNA]) - rx[RX_EAR] * invT;
+    double q = exp(lnkf) * cC[a0];
+    if (a1 != kNone) q *= cC[a1];
+    double rof = 1.0;
+    if (ri.z) {
+      // dG/RT = sum nu G/RT;  ln kr = ln kf - ln K,  ln K = dN ln(P_atm/RT) - dG/RT
+      double dG = cG[p0] - cG[a0];
+      if (a1 != kNone) dG -= cG[a1];
+      if (p1 != kNone) dG += cG[p1];
+      double rev = exp(lnkf + dG - (double)ri.y * lnPref) * cC[p0];
+      if (p1 != kNone) rev *= cC[p1];
+      q -= rev;
+      if (L.dft_on) {
+        cHist[ktap * Rrev + ri.w] = q;  // raw rate; times h once h is known (Eq. 8)
+        rof = cRof[ri.w];
+      }
+    }
+    cQ[r] = q * rof;
+  }
+  __syncwarp();
+
+  // production rates, dY/dt, adiabatic dT/dt terms and the limiter (Eqs. 1-5)
+  const double invRho = 1.0 / rho;
+  double hwp = 0.0, num = 1.0, den = 0.0;
+  for (int i = l; i < S; i += G) {
+    double wd = 0.0;
+    for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
+      const int e = tb.gent[k];
+      wd = fma((double)((e & 15) - 8), cQ[e >> 4], wd);
+    }
+    const double ri = tb.sp[i * SP_STRIDE + SP_W] * wd * invRho;
+    hwp = fma(cH[i], wd, hwp);
+    cC[i] = ri;  // concentrations are no longer needed: keep dY/dt here
+    const double rstar = fmax(-ri, 1.0e-30);
+    const double Yi = cY[i];
+    const double ystar = (Yi < 1.0e-20) ? 1.0 : 0.9 * Yi;
+    const double nn = fmin(L.y_step_max, ystar);
+    if (den == 0.0 || nn * den < num * rstar) { num = nn; den = rstar; }
+  }
+  const double hw = group_sum<G>(hwp);
+  group_min_frac<G>(num, den);
+  const double dTdt = -(T * hw) / (rho * cpsum);
+  double h = fmin(num / den, L.dt * L.delta_max);
+  const bool last = (h >= st.t_rem);
+  if (last) h = st.t_rem;
+
+  // DFT ringing detection and damping (Eqs. 8-13) on reversible reactions
+  if (L.dft_on) {
+    const bool full = (st.nhist + 1 >= N);
+    for (int w = l; w < Rrev; w += G) {
+      const double x = cHist[ktap * Rrev + w] * h;
+      cHist[ktap * Rrev + w] = x;
+      double rof = cRof[w];
+      if (full) {
+        double s = 0.0;
+        for (int m = 0; m < N; ++m) s += cHist[m * Rrev + w];  // storage order, as Eq. 9's sum
+        const double D0 = fabs(s);
+        double rstar = L.r_fac;
+        if (D0 < L.tol_freq) {  // only then can Eq. 12 damp: evaluate the high bins
+          double maxhf = 0.0;
+          for (int bb = 0; bb < L.n_hi_bins; ++bb) {
+            const double* c = tb.tw + bb * 2 * N;
+            double re = 0.0, im = 0.0;
+            for (int m = 0; m < N; ++m) {
+              const double xm = cHist[m * Rrev + w];
+              re = fma(xm, c[m], re);
+              im = fma(xm, c[N + m], im);
+            }
+            maxhf = fmax(maxhf, hypot(re, im));
+          }
+          if (D0 < L.tol_ring * maxhf) rstar = 1.0 / L.r_fac;
+        }
+        rof = fmax(fmin(rof * rstar, 1.0), L.rof_min);
+      } else {
+        rof = fmin(rof * L.r_fac, 1.0);
+      }
+      cRof[w] = rof;
+    }
+    st.nhist += 1;
+  }
+
+  // forward Euler (Eq. 18)
+  bool bad = false;
+  for (int i = l; i < S; i += G) {
+    const double y = fma(h, cC[i], cY[i]);
+    cY[i] = y;
+    bad = bad || !isfinite(y);
+  }
+  st.T = fma(h, dTdt, T);
+  st.t_rem -= h;
+  st.it += 1;
+  bad = group_any<G>(bad) || !isfinite(st.T);
+  __syncwarp();
+  if (bad) return 2;                           // STEV_CELL_NONFINITE
+  if (st.T < 200.0 || st.T > 6000.0) return 3;  // STEV_CELL_TRANGE
+  if (last) return 0;                          // STEV_CELL_OK
+  if (st.it >= L.max_iters) return 1;          // STEV_CELL_MAXITER
+  return -1;
+}
+
+// ---------------------------------------------------------- persistent kernel
+template <int G>
+__global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = L.S, R = L.R;
+  // stage the mechanism tables once per CTA
+  double* s_sp = reinterpret_cast<double*>(smem_raw);
+  double* s_rx = s_sp + S * SP_STRIDE;
+  int4* s_ri = reinterpret_cast<int4*>(s_rx + R * RX_STRIDE);
+  double* s_tw = reinterpret_cast<double*>(s_ri + R);
+  int* s_gptr = reinterpret_cast<int*>(s_tw + L.n_hi_bins * 2 * L.dft_n);
+  int* s_gent = s_gptr + S + 1;
+  for (int t = threadIdx.x; t < S * SP_STRIDE; t += blockDim.x) s_sp[t] = L.sp_tab[t];
+  for (int t = threadIdx.x; t < R * RX_STRIDE; t += blockDim.x) s_rx[t] = L.rx_tab[t];
+  for (int t = threadIdx.x; t < R; t += blockDim.x) s_ri[t] = L.rx_idx[t];
+  for (int t = threadIdx.x; t < L.n_hi_bins * 2 * L.dft_n; t += blockDim.x) s_tw[t] = L.dft_tw[t];
+  for (int t = threadIdx.x; t <= S; t += blockDim.x) s_gptr[t] = L.g_ptr[t];
+  for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
+  __syncthreads();
+  const Tables tb{s_sp, s_rx, s_ri, s_gptr, s_gent, s_tw};
+
+  // this group's cell area
+  const int group = threadIdx.x / G;
+  const int l = threadIdx.x % G;
+  const int lane = threadIdx.x & 31;
+  const size_t tables = table_smem_bytes(S, R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t cell_bytes = cell_smem_bytes_fp64(S, R, L.Rrev, L.dft_n);
+  double* cY = reinterpret_cast<double*>(smem_raw + tables + (size_t)group * cell_bytes);
+  double* cC = cY + S;
+  double* cG = cC + S;
+  double* cH = cG + S;
+  double* cQ = cH + S;
+  double* cHist = cQ + R;
+  double* cRof = cHist + L.dft_n * L.Rrev;
+  for (int i = l; i < S; i += G) cY[i] = 0.0;
+
+  const unsigned long long n = (unsigned long long)L.n_cells;
+  const int leader = lane & ~(G - 1);  // lane of this group's leader in the warp
+  CellState st;
+  st.cell = -1;
+  st.T = 1000.0;
+  st.P = kPatm;
+  st.t_rem = 1.0;
+  st.it = 0;
+  st.nhist = 0;
+  bool exhausted = false;  // warp-uniform
+  while (true) {
+    // refill: one bit per group that needs a cell, one atomic per warp
+    const unsigned need = __ballot_sync(0xffffffffu, (lane == leader) && st.cell < 0);
+    if (need != 0u && !exhausted) {
+      const unsigned cnt = __popc(need);
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(L.counter, (unsigned long long)cnt);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base + cnt >= n) exhausted = true;
+      if (st.cell < 0) {
+        const unsigned long long c = base + __popc(need & ((1u << leader) - 1u));
+        if (c < n) {
+          st.cell = (long long)c;
+          st.T = L.T[c];
+          st.P = L.P[c];
+          st.t_rem = L.dt;
+          st.it = 0;
+          st.nhist = 0;
+          if (L.y_soa)
+            for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
+          else
+            for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)c * S + i];
+          for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0;  // Eq. 11
+        }
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
+    const int outcome = step_fp64<G>(L, tb, cY, cC, cG, cH, cQ, cHist, cRof, l, st);
+    if (st.cell >= 0 && outcome >= 0) {
+      const long long c = st.cell;
+      if (l == 0) {
+        L.T_out[c] = st.T;
+        L.iters[c] = st.it;
+        L.status[c] = (unsigned char)outcome;
+      }
+      if (L.y_soa)
+        for (int i = l; i < S; i += G) L.Y_out[(long long)i * L.n_cells + c] = cY[i];
+      else
+        for (int i = l; i < S; i += G) L.Y_out[c * S + i] = cY[i];
+      st.cell = -1;
+    }
+  }
+}
+
+}  // namespace stev
