@@ -65,7 +65,14 @@ class _Opts(ctypes.Structure):
 PROBES = {"kf_up": ["-DORACLE_KF_SCALE=(1.0+2.220446049250313e-16)"],
           "kf_down": ["-DORACLE_KF_SCALE=(1.0-1.1102230246251565e-16)"],
           "K_up": ["-DORACLE_K_SCALE=(1.0+1.4210854715202004e-14)"],
-          "K_down": ["-DORACLE_K_SCALE=(1.0-1.4210854715202004e-14)"]}
+          "K_down": ["-DORACLE_K_SCALE=(1.0-1.4210854715202004e-14)"],
+          # single-precision-sized changes: kf by 2^-22, K by 2^-18
+          "kf32_up": ["-DORACLE_KF_SCALE=(1.0+2.384185791015625e-07)"],
+          "kf32_down": ["-DORACLE_KF_SCALE=(1.0-2.384185791015625e-07)"],
+          "K32_up": ["-DORACLE_K_SCALE=(1.0+3.814697265625e-06)"],
+          "K32_down": ["-DORACLE_K_SCALE=(1.0-3.814697265625e-06)"]}
+PROBE_LEVELS = {"fp64": ("kf_up", "kf_down", "K_up", "K_down"),
+                "fp32": ("kf32_up", "kf32_down", "K32_up", "K32_down")}
 
 
 def _lib_path(probe: Optional[str]) -> str:
@@ -239,18 +246,21 @@ def solve(mech, T, P, Y, dt: float, n_threads: Optional[int] = None,
     return To, Yo, iters, status
 
 
-def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] = None, **opts):
+def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] = None,
+                 level: str = "fp64", **opts):
     """Per-cell spread of the final state under rounding-size rate changes.
 
     Returns (base_result, dY_spread[cells], dT_spread[cells]): the largest
     |change| of Y (over species) and of T between the default build and the
-    probe builds (every kf off by one ulp, every K off by 64 ulp).  A cell whose spread is far below a tolerance is
+    probe builds of the given level: "fp64" changes every kf by one ulp and
+    every K by 64 ulp; "fp32" by 2^-22 and 2^-18, the size of the rounding
+    of a single-precision rate and of its exponent.  A cell whose spread is far below a tolerance is
     well-conditioned at that tolerance."""
     if base is None:
         base = solve(mech, T, P, Y, dt, n_threads=n_threads, **opts)
     dY = np.zeros(len(T))
     dT = np.zeros(len(T))
-    for p in PROBES:
+    for p in PROBE_LEVELS[level]:
         r = solve(mech, T, P, Y, dt, n_threads=n_threads, probe=p, **opts)
         dY = np.maximum(dY, np.abs(r[1] - base[1]).max(axis=1))
         dT = np.maximum(dT, np.abs(r[0] - base[0]))

@@ -14,6 +14,7 @@
 #include "../../include/stev.h"
 #include "stev_device.cuh"
 #include "stev_fp64.cuh"
+#include "stev_mixed.cuh"
 
 using namespace stev;
 
@@ -50,6 +51,9 @@ struct stev_mechanism {
   int* d_gptr = nullptr;
   int* d_gent = nullptr;
   double* d_tw = nullptr;
+  float* d_spf = nullptr;  // float tables of the mixed kernel
+  float4* d_rxf = nullptr;
+  float* d_twf = nullptr;
   // launch configuration of the persistent kernel
   int G = 32;              // lanes per cell
   int block = 0, grid = 0; // threads per CTA, CTAs
@@ -94,13 +98,14 @@ static stev_status check_options(const stev_options* o) {
   if (o->max_iters < 1) return fail(STEV_EINVAL, "max_iters must be >= 1");
   if (o->precision != STEV_FP64 && o->precision != STEV_MIXED) return fail(STEV_EINVAL, "unknown precision");
   if (o->thermo != STEV_THERMO_POLY && o->thermo != STEV_THERMO_MLP) return fail(STEV_EINVAL, "unknown thermo mode");
-  if (o->precision == STEV_MIXED || o->thermo == STEV_THERMO_MLP)
-    return fail(STEV_EINVAL, "precision/thermo mode not available in this build");
+  if (o->thermo == STEV_THERMO_MLP)
+    return fail(STEV_EINVAL, "thermo mode not available in this build");
   return STEV_OK;
 }
 
 static void free_mech(stev_mechanism* m) {
-  void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_counter,
+  void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
+                  m->d_twf, m->d_counter,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -109,7 +114,14 @@ static void free_mech(stev_mechanism* m) {
 
 typedef void (*KernelFn)(Launch);
 
-static KernelFn fp64_kernel(int G) {
+static KernelFn select_kernel(int precision, int G) {
+  if (precision == STEV_MIXED) {
+    switch (G) {
+      case 8: return stev_mixed_kernel<8>;
+      case 16: return stev_mixed_kernel<16>;
+      default: return stev_mixed_kernel<32>;
+    }
+  }
   switch (G) {
     case 8: return stev_fp64_kernel<8>;
     case 16: return stev_fp64_kernel<16>;
@@ -133,17 +145,21 @@ static stev_status configure(stev_mechanism* m) {
   CUDA_TRY(cudaGetDeviceProperties(&prop, m->device));
   m->G = choose_group(m->S, m->R);
   const int G = m->G;
-  const size_t tables = table_smem_bytes(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n);
-  const size_t cell = cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
+  const bool mixed = m->opt.precision == STEV_MIXED;
+  const size_t tables =
+      mixed ? table_smem_bytes_mixed(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n)
+            : table_smem_bytes(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n);
+  const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n)
+                            : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
   const size_t limit = prop.sharedMemPerBlockOptin;
   if (tables + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
   int cells = (int)((limit - tables) / cell);
-  cells = std::min(cells, kMaxBlock / G);
+  cells = std::min(cells, (mixed ? kMaxBlockMixed : kMaxBlock) / G);
   const int per_warp = 32 / G;
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
   const size_t smem = tables + (size_t)cells * cell;
-  KernelFn k = fp64_kernel(G);
+  KernelFn k = select_kernel(m->opt.precision, G);
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cells * G, smem));
@@ -233,6 +249,7 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
     e[RX_LNA] = std::log(A[r]);
     e[RX_BETA] = beta[r];
     e[RX_EAR] = Ea[r] / kRu;
+    e[RX_DN] = (double)(np - nr);
     const int a0 = reac[0], a1 = nr > 1 ? reac[1] : kNone;
     const int p0 = prod[0], p1 = np > 1 ? prod[1] : kNone;
     ri[r].x = a0 | (a1 << 8) | (p0 << 16) | (p1 << 24);
@@ -284,6 +301,33 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
   TRY_OR_FREE(upload((void**)&m->d_rx, rx.data(), rx.size() * sizeof(double)));
   TRY_OR_FREE(upload((void**)&m->d_ri, ri.data(), ri.size() * sizeof(int4)));
   TRY_OR_FREE(upload((void**)&m->d_tw, tw.data(), tw.size() * sizeof(double)));
+  // float tables of the mixed kernel (log2 space for the MUFU exponentials)
+  std::vector<float> spf((size_t)S * SPF_STRIDE, 0.0f);
+  for (int i = 0; i < S; ++i) {
+    const double* e = &sp[(size_t)i * SP_STRIDE];
+    float* f = &spf[(size_t)i * SPF_STRIDE];
+    f[SPF_W] = (float)e[SP_W];
+    f[SPF_INVW] = (float)e[SP_INVW];
+    for (int rg = 0; rg < 2; ++rg) {
+      const double* b = e + (rg == 0 ? SP_LOW : SP_HIGH);
+      float* bf = f + (rg == 0 ? SPF_LOW : SPF_HIGH);
+      for (int k = 0; k < 6; ++k) bf[BF_A0 + k] = (float)b[B_A0 + k];
+      bf[BF_H1] = (float)b[B_H1];
+      bf[BF_H2] = (float)b[B_H2];
+      bf[BF_H3] = (float)b[B_H3];
+      bf[BF_H4] = (float)b[B_H4];
+    }
+  }
+  std::vector<float4> rxf(R);
+  for (int r = 0; r < R; ++r) {
+    const double* e = &rx[(size_t)r * RX_STRIDE];
+    rxf[r] = make_float4((float)(e[RX_LNA] * kLog2e), (float)e[RX_BETA],
+                         (float)(e[RX_EAR] * kLog2e), (float)e[RX_DN]);
+  }
+  std::vector<float> twf(tw.begin(), tw.end());
+  TRY_OR_FREE(upload((void**)&m->d_spf, spf.data(), spf.size() * sizeof(float)));
+  TRY_OR_FREE(upload((void**)&m->d_rxf, rxf.data(), rxf.size() * sizeof(float4)));
+  TRY_OR_FREE(upload((void**)&m->d_twf, twf.data(), twf.size() * sizeof(float)));
   TRY_OR_FREE(upload((void**)&m->d_gptr, gptr.data(), gptr.size() * sizeof(int)));
   TRY_OR_FREE(upload((void**)&m->d_gent, gent.data(), gent.size() * sizeof(int)));
   TRY_OR_FREE(configure(m));
@@ -313,6 +357,11 @@ extern "C" stev_status stev_mechanism_set_options(stev_mechanism* m, const stev_
     m->d_tw = nullptr;
     CUDA_TRY(cudaMalloc(&m->d_tw, tw.size() * sizeof(double)));
     CUDA_TRY(cudaMemcpy(m->d_tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<float> twf(tw.begin(), tw.end());
+    if (m->d_twf) cudaFree(m->d_twf);
+    m->d_twf = nullptr;
+    CUDA_TRY(cudaMalloc(&m->d_twf, twf.size() * sizeof(float)));
+    CUDA_TRY(cudaMemcpy(m->d_twf, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice));
     m->n_hi_bins = nb;
   }
   m->opt = *opt;
@@ -339,6 +388,9 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   L.g_ptr = m->d_gptr;
   L.g_ent = m->d_gent;
   L.dft_tw = m->d_tw;
+  L.sp_tab_f = m->d_spf;
+  L.rx_tab_f = m->d_rxf;
+  L.dft_tw_f = m->d_twf;
   L.n_hi_bins = m->n_hi_bins;
   L.dft_n = m->opt.dft_n;
   L.dft_on = m->opt.dft_on;
@@ -372,7 +424,7 @@ static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, co
 
 static stev_status launch_persistent(stev_mechanism* m, const Launch& L, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned long long), s));
-  fp64_kernel(m->G)<<<m->grid, m->block, m->smem, s>>>(L);
+  select_kernel(m->opt.precision, m->G)<<<m->grid, m->block, m->smem, s>>>(L);
   CUDA_TRY(cudaGetLastError());
   return STEV_OK;
 }

@@ -8,7 +8,7 @@
 //              H/RT = a0 + T(a1/2 + T(a2/3 + T(a3/4 + T a4/5))) + a5/T (Eq. 16)
 //              G/RT = H/RT - S/R
 //                   = a0(1 - lnT) - T(a1/2 + T(a2/6 + T(a3/12 + T a4/20))) + a5/T - a6
-//   reaction : lnA, beta, Ea/R (Eq. 29 in log form) and an int4 with the
+//   reaction : lnA, beta, Ea/R (Eq. 29 in log form), dN, and an int4 with the
 //              packed species slots (two reactant, two product, 0xFF = none;
 //              a species of order 2 fills both slots), dN = sum(nu), the
 //              reversible flag and the reaction's index among reversible ones.
@@ -28,15 +28,23 @@ constexpr int kMaxGatherEntries = 4 * kMaxReactions;
 constexpr double kRu = 8.314462618;     // J/(mol K)
 constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
 constexpr int kNone = 0xFF;
-constexpr int kMaxBlock = 512;       // threads per CTA of the persistent kernels
+constexpr int kMaxBlock = 512;       // threads per CTA of the FP64 persistent kernel
+constexpr int kMaxBlockMixed = 768;  // threads per CTA of the mixed persistent kernel
 
 enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
        B_SIZE };
-enum { RX_LNA = 0, RX_BETA = 1, RX_EAR = 2, RX_STRIDE = 4 };
+enum { RX_LNA = 0, RX_BETA = 1, RX_EAR = 2, RX_DN = 3, RX_STRIDE = 4 };
+// float species table of the mixed kernel: W, 1/W, pad, pad, then per range
+// a0..a5 and the H/RT coefficients a1/2..a4/5
+enum { SPF_W = 0, SPF_INVW = 1, SPF_LOW = 4, SPF_HIGH = 14, SPF_STRIDE = 24 };
+enum { BF_A0 = 0, BF_A1, BF_A2, BF_A3, BF_A4, BF_A5, BF_H1, BF_H2, BF_H3, BF_H4, BF_SIZE };
 
-// gather entry: reaction index * 16 + (nu + 8)
+// gather entry: reaction index * 16 + (nu + 8); the stoichiometric factor is
+// read back from kNuOf[] so that no integer-to-double conversion is needed
 __host__ __device__ inline int gather_pack(int r, int nu) { return r * 16 + (nu + 8); }
+__constant__ double kNuOf[16] = {0, 0, 0, 0, 0, 0, -2.0, -1.0, 0, 1.0, 2.0, 0, 0, 0, 0, 0};
+__constant__ float kNuOfF[16] = {0, 0, 0, 0, 0, 0, -2.0f, -1.0f, 0, 1.0f, 2.0f, 0, 0, 0, 0, 0};
 
 // Everything a launch needs, passed by value.
 struct Launch {
@@ -48,6 +56,9 @@ struct Launch {
   const int* g_ptr;       // [S+1] species-major gather lists
   const int* g_ent;       // [n_gather]
   const double* dft_tw;   // [n_hi_bins][2][dft_n]: cos, sin of -2 pi j m / N
+  const float* sp_tab_f;  // [S][SPF_STRIDE]        (mixed kernel)
+  const float4* rx_tab_f; // [R] lg2 A, beta, Ea/R log2 e, dN (mixed kernel)
+  const float* dft_tw_f;  // float twiddles          (mixed kernel)
   int n_hi_bins;
   // options (Secs. 2.1-2.3)
   int dft_n, dft_on, max_iters;
@@ -79,6 +90,21 @@ __host__ __device__ inline size_t table_smem_bytes(int S, int R, int n_gather, i
 // H/RT (S each), effective rates (R), history [N][Rrev] and rOF (Rrev).
 __host__ __device__ inline size_t cell_smem_bytes_fp64(int S, int R, int Rrev, int dft_n) {
   size_t b = ((size_t)4 * S + R + (size_t)dft_n * Rrev + Rrev) * 8;
+  return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gather, int n_hi_bins,
+                                                         int dft_n) {
+  size_t b = (size_t)S * SP_STRIDE * 8 + (size_t)R * 16 + (size_t)R * 16 +
+             (size_t)S * SPF_STRIDE * 4 + (size_t)n_hi_bins * 2 * dft_n * 4 +
+             (size_t)(S + 1 + n_gather) * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+// Mixed kernel cell: Y and G/RT log2 e in FP64 (S each); C, H/RT (S each),
+// rates (R), history [N][Rrev] and rOF (Rrev) in FP32.
+__host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n) {
+  size_t b = (size_t)16 * S + ((size_t)2 * S + R + (size_t)dft_n * Rrev + Rrev) * 4;
   return (b + 15) & ~(size_t)15;
 }
 

@@ -23,54 +23,9 @@
 // the warp exits when none of its groups holds a cell.  The kernel has no
 // waits: every loop is bounded by the mechanism size or max_iters.
 #pragma once
-#include "stev_device.cuh"
+#include "stev_common.cuh"
 
 namespace stev {
-
-template <int G>
-__device__ __forceinline__ double group_sum(double v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
-  return v;
-}
-
-// Minimum of num/den over the group (den > 0; den == 0 encodes +inf), with a
-// symmetric tie-break so that every lane keeps the same pair.
-template <int G>
-__device__ __forceinline__ void group_min_frac(double& num, double& den) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const double n2 = __shfl_xor_sync(0xffffffffu, num, o, G);
-    const double d2 = __shfl_xor_sync(0xffffffffu, den, o, G);
-    const double a = n2 * den, b = num * d2;
-    const bool take = (a < b) || (a == b && (n2 < num || (n2 == num && d2 < den)));
-    if (take) { num = n2; den = d2; }
-  }
-}
-
-template <int G>
-__device__ __forceinline__ bool group_any(bool v) {
-  const unsigned b = __ballot_sync(0xffffffffu, v);
-  const int base = (threadIdx.x & 31) & ~(G - 1);
-  const unsigned m = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
-  return (b & m) != 0u;
-}
-
-struct CellState {
-  long long cell;   // -1 when the group has no cell
-  double T, P, t_rem;
-  int it;
-  int nhist;
-};
-
-struct Tables {
-  const double* sp;
-  const double* rx;
-  const int4* ri;
-  const int* gptr;
-  const int* gent;
-  const double* tw;
-};
 
 // One STEV iteration of one cell by its group (Secs. 2.1-2.3, Eq. 18).
 // Returns -1 to continue, else the STEV_CELL_* outcome.
@@ -125,7 +80,7 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
       double dG = cG[p0] - cG[a0];
       if (a1 != kNone) dG -= cG[a1];
       if (p1 != kNone) dG += cG[p1];
-      double rev = exp(lnkf + dG - (double)ri.y * lnPref) * cC[p0];
+      double rev = exp(fma(-rx[RX_DN], lnPref, lnkf + dG)) * cC[p0];
       if (p1 != kNone) rev *= cC[p1];
       q -= rev;
       if (L.dft_on) {
@@ -144,7 +99,7 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
     double wd = 0.0;
     for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
       const int e = tb.gent[k];
-      wd = fma((double)((e & 15) - 8), cQ[e >> 4], wd);
+      wd = fma(kNuOf[e & 15], cQ[e >> 4], wd);
     }
     const double ri = tb.sp[i * SP_STRIDE + SP_W] * wd * invRho;
     hwp = fma(cH[i], wd, hwp);
@@ -174,19 +129,31 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
         for (int m = 0; m < N; ++m) s += cHist[m * Rrev + w];  // storage order, as Eq. 9's sum
         const double D0 = fabs(s);
         double rstar = L.r_fac;
-        if (D0 < L.tol_freq) {  // only then can Eq. 12 damp: evaluate the high bins
-          double maxhf = 0.0;
-          for (int bb = 0; bb < L.n_hi_bins; ++bb) {
-            const double* c = tb.tw + bb * 2 * N;
-            double re = 0.0, im = 0.0;
-            for (int m = 0; m < N; ++m) {
-              const double xm = cHist[m * Rrev + w];
-              re = fma(xm, c[m], re);
-              im = fma(xm, c[N + m], im);
+        if (D0 < L.tol_freq) {  // only then can Eq. 12 damp
+          // every |X_j| <= sum |x_m|: a window with D0 >= Tol_ring sum|x_m|
+          // cannot ring (Eq. 10), so its high bins are not needed
+          double a = 0.0;
+          for (int m = 0; m < N; ++m) a += fabs(cHist[m * Rrev + w]);
+          if (D0 < L.tol_ring * a) {
+            // D0 < Tol_ring max|X_j|, compared as squares in units of sum|x_m|
+            // (every scaled magnitude is <= 1, so the squares cannot underflow)
+            const double inv = 1.0 / a;
+            double max2 = 0.0;
+            for (int bb = 0; bb < L.n_hi_bins; ++bb) {
+              const double* c = tb.tw + bb * 2 * N;
+              double re = 0.0, im = 0.0;
+              for (int m = 0; m < N; ++m) {
+                const double xm = cHist[m * Rrev + w];
+                re = fma(xm, c[m], re);
+                im = fma(xm, c[N + m], im);
+              }
+              re *= inv;
+              im *= inv;
+              max2 = fmax(max2, fma(re, re, im * im));
             }
-            maxhf = fmax(maxhf, hypot(re, im));
+            const double d = D0 * inv;
+            if (d * d < L.tol_ring * L.tol_ring * max2) rstar = 1.0 / L.r_fac;
           }
-          if (D0 < L.tol_ring * maxhf) rstar = 1.0 / L.r_fac;
         }
         rof = fmax(fmin(rof * rstar, 1.0), L.rof_min);
       } else {
@@ -240,7 +207,6 @@ __global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
   // this group's cell area
   const int group = threadIdx.x / G;
   const int l = threadIdx.x % G;
-  const int lane = threadIdx.x & 31;
   const size_t tables = table_smem_bytes(S, R, L.n_gather, L.n_hi_bins, L.dft_n);
   const size_t cell_bytes = cell_smem_bytes_fp64(S, R, L.Rrev, L.dft_n);
   double* cY = reinterpret_cast<double*>(smem_raw + tables + (size_t)group * cell_bytes);
@@ -253,7 +219,6 @@ __global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
   for (int i = l; i < S; i += G) cY[i] = 0.0;
 
   const unsigned long long n = (unsigned long long)L.n_cells;
-  const int leader = lane & ~(G - 1);  // lane of this group's leader in the warp
   CellState st;
   st.cell = -1;
   st.T = 1000.0;
@@ -263,32 +228,21 @@ __global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
   st.nhist = 0;
   bool exhausted = false;  // warp-uniform
   while (true) {
-    // refill: one bit per group that needs a cell, one atomic per warp
-    const unsigned need = __ballot_sync(0xffffffffu, (lane == leader) && st.cell < 0);
-    if (need != 0u && !exhausted) {
-      const unsigned cnt = __popc(need);
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(L.counter, (unsigned long long)cnt);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base + cnt >= n) exhausted = true;
-      if (st.cell < 0) {
-        const unsigned long long c = base + __popc(need & ((1u << leader) - 1u));
-        if (c < n) {
-          st.cell = (long long)c;
-          st.T = L.T[c];
-          st.P = L.P[c];
-          st.t_rem = L.dt;
-          st.it = 0;
-          st.nhist = 0;
-          if (L.y_soa)
-            for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
-          else
-            for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)c * S + i];
-          for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0;  // Eq. 11
-        }
-      }
-      __syncwarp();
+    const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
+    if (c >= 0) {
+      st.cell = c;
+      st.T = L.T[c];
+      st.P = L.P[c];
+      st.t_rem = L.dt;
+      st.it = 0;
+      st.nhist = 0;
+      if (L.y_soa)
+        for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
+      else
+        for (int i = l; i < S; i += G) cY[i] = L.Y[c * S + i];
+      for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0;  // Eq. 11
     }
+    __syncwarp();
     if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
     const int outcome = step_fp64<G>(L, tb, cY, cC, cG, cH, cQ, cHist, cRof, l, st);
     if (st.cell >= 0 && outcome >= 0) {

@@ -1,0 +1,276 @@
+// Mixed-precision STEV: rates in FP32, state update and Gibbs exponent in FP64.
+//
+// Same structure as the FP64 kernel (a group of G lanes per cell, all cell
+// state in shared memory, species-major gather, ballot/popcount refill).
+// What changes is the arithmetic:
+//   FP64  Y and T (the forward Euler update of Eq. 18), t_rem and h, G/RT of
+//         every species and the per-reaction Gibbs difference
+//         dG/RT - dN ln(P_atm/RT) that sets K (Eq. 30), whose cancellation of
+//         large terms is where precision matters;
+//   FP32  mixture, cp/R and H/RT (Eqs. 15-16), gamma and concentrations
+//         (Eqs. 6-7), forward and reverse rate constants (exponentials on the
+//         MUFU unit in base 2: k = 2^(log2 k)), rates of progress and rOF
+//         (Eq. 14), production rates, dT/dt, the limiter (Eqs. 1-5) and the
+//         ringing history and DFT test (Eqs. 8-13).
+#pragma once
+#include "stev_common.cuh"
+
+namespace stev {
+
+constexpr double kLog2e = 1.4426950408889634;
+
+__device__ __forceinline__ float ex2f(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+struct TablesF {
+  const double* sp;   // double species table (G/RT coefficients)
+  const float* spf;   // float species table
+  const float4* rxf;  // lg2 A, beta, Ea/R log2 e, dN
+  const int4* ri;
+  const int* gptr;
+  const int* gent;
+  const float* tw;    // float twiddles
+};
+
+template <int G>
+__device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
+                                          double* cG2, float* cC, float* cH, float* cQ,
+                                          float* cHist, float* cRof, int l, CellState& st) {
+  const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
+  const double T = st.T;
+  const double lnT = log(T);        // FP64: feeds G/RT
+  const double invT = 1.0 / T;
+  const float Tf = (float)T;
+  const float invTf = (float)invT;
+  const float lg2Tf = (float)(lnT * kLog2e);
+
+  // mixture (FP32)
+  float part = 0.0f;
+  for (int i = l; i < S; i += G) part = fmaf((float)cY[i], tb.spf[i * SPF_STRIDE + SPF_INVW], part);
+  const float sumYW = group_sum<G>(part);
+  const float rho = (float)st.P / ((float)kRu * Tf * sumYW);
+
+  // thermo: cp/R, H/RT in FP32; G/RT in FP64 (in log2 units, G/RT * log2 e)
+  float cpp = 0.0f;
+  for (int i = l; i < S; i += G) {
+    const float* spf = tb.spf + i * SPF_STRIDE;
+    const double* sp = tb.sp + i * SP_STRIDE;
+    const bool lo = T < sp[SP_TSPLIT];
+    const float* b = spf + (lo ? SPF_LOW : SPF_HIGH);
+    const double* bd = sp + (lo ? SP_LOW : SP_HIGH);
+    const float Yi = (float)cY[i];
+    const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf, b[BF_A1]), Tf,
+                           b[BF_A0]);
+    const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
+    cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+    const double gp = fma(fma(fma(bd[B_G4], T, bd[B_G3]), T, bd[B_G2]), T, bd[B_H1]);
+    cG2[i] = (fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T) * kLog2e;
+    cpp = fmaf(Yi * cpR, spf[SPF_INVW], cpp);
+    const float y = fmaxf(Yi, 0.0f);
+    const float ys = (L.alpha > 0.0) ? y * __fdividef(y, (float)L.alpha + y) : y;
+    cC[i] = rho * ys * spf[SPF_INVW];
+  }
+  const float cpsum = group_sum<G>(cpp);
+  __syncwarp();
+
+  // rates of progress: kf = 2^(lg2 A + beta lg2 T - Ea/R log2e / T) (FP32);
+  // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e formed in FP64
+  const double lg2Pref = (L.ln_patm_over_ru - lnT) * kLog2e;
+  const int ktap = st.nhist % N;
+  for (int r = l; r < R; r += G) {
+    const float4 rx = tb.rxf[r];
+    const int4 ri = tb.ri[r];
+    const int a0 = ri.x & 0xFF, a1 = (ri.x >> 8) & 0xFF;
+    const int p0 = (ri.x >> 16) & 0xFF, p1 = (ri.x >> 24) & 0xFF;
+    const float lg2kf = fmaf(rx.y, lg2Tf, rx.x) - rx.z * invTf;
+    float q = ex2f(lg2kf) * cC[a0];
+    if (a1 != kNone) q *= cC[a1];
+    float rof = 1.0f;
+    if (ri.z) {
+      double dG = cG2[p0] - cG2[a0];
+      if (a1 != kNone) dG -= cG2[a1];
+      if (p1 != kNone) dG += cG2[p1];
+      const float x = (float)fma(-(double)rx.w, lg2Pref, dG);
+      float rev = ex2f(lg2kf + x) * cC[p0];
+      if (p1 != kNone) rev *= cC[p1];
+      q -= rev;
+      if (L.dft_on) {
+        cHist[ktap * Rrev + ri.w] = q;
+        rof = cRof[ri.w];
+      }
+    }
+    cQ[r] = q * rof;
+  }
+  __syncwarp();
+
+  // production rates, dY/dt, dT/dt terms and the limiter (FP32)
+  const float invRho = 1.0f / rho;
+  float hwp = 0.0f, tmin = INFINITY;
+  for (int i = l; i < S; i += G) {
+    float wd = 0.0f;
+    for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
+      const int e = tb.gent[k];
+      wd = fmaf(kNuOfF[e & 15], cQ[e >> 4], wd);
+    }
+    const float ri = tb.spf[i * SPF_STRIDE + SPF_W] * wd * invRho;
+    hwp = fmaf(cH[i], wd, hwp);
+    cC[i] = ri;
+    const float rstar = fmaxf(-ri, 1.0e-30f);
+    const float Yi = (float)cY[i];
+    const float ystar = (Yi < 1.0e-20f) ? 1.0f : 0.9f * Yi;
+    tmin = fminf(tmin, __fdividef(fminf((float)L.y_step_max, ystar), rstar));
+  }
+  const float hw = group_sum<G>(hwp);
+  tmin = group_min<G>(tmin);
+  const float dTdt = -(Tf * hw) / (rho * cpsum);
+  double h = fmin((double)tmin, L.dt * L.delta_max);
+  const bool last = (h >= st.t_rem);
+  if (last) h = st.t_rem;
+  const float hf = (float)h;
+
+  // ringing detection and damping (Eqs. 8-13), FP32
+  if (L.dft_on) {
+    const bool full = (st.nhist + 1 >= N);
+    const float tol_freq = (float)L.tol_freq, tol_ring = (float)L.tol_ring;
+    const float r_fac = (float)L.r_fac;
+    for (int w = l; w < Rrev; w += G) {
+      const float x = cHist[ktap * Rrev + w] * hf;
+      cHist[ktap * Rrev + w] = x;
+      float rof = cRof[w];
+      if (full) {
+        float s = 0.0f;
+        for (int m = 0; m < N; ++m) s += cHist[m * Rrev + w];
+        const float D0 = fabsf(s);
+        float rstar = r_fac;
+        if (D0 < tol_freq) {
+          float a = 0.0f;
+          for (int m = 0; m < N; ++m) a += fabsf(cHist[m * Rrev + w]);
+          if (D0 < tol_ring * a) {
+            const float inv = 1.0f / a;
+            float max2 = 0.0f;
+            for (int bb = 0; bb < L.n_hi_bins; ++bb) {
+              const float* c = tb.tw + bb * 2 * N;
+              float re = 0.0f, im = 0.0f;
+              for (int m = 0; m < N; ++m) {
+                const float xm = cHist[m * Rrev + w];
+                re = fmaf(xm, c[m], re);
+                im = fmaf(xm, c[N + m], im);
+              }
+              re *= inv;
+              im *= inv;
+              max2 = fmaxf(max2, fmaf(re, re, im * im));
+            }
+            const float d = D0 * inv;
+            if (d * d < tol_ring * tol_ring * max2) rstar = 1.0f / r_fac;
+          }
+        }
+        rof = fmaxf(fminf(rof * rstar, 1.0f), (float)L.rof_min);
+      } else {
+        rof = fminf(rof * r_fac, 1.0f);
+      }
+      cRof[w] = rof;
+    }
+    st.nhist += 1;
+  }
+
+  // forward Euler in FP64 (Eq. 18)
+  bool bad = false;
+  for (int i = l; i < S; i += G) {
+    const double y = fma(h, (double)cC[i], cY[i]);
+    cY[i] = y;
+    bad = bad || !isfinite(y);
+  }
+  st.T = fma(h, (double)dTdt, T);
+  st.t_rem -= h;
+  st.it += 1;
+  bad = group_any<G>(bad) || !isfinite(st.T);
+  __syncwarp();
+  if (bad) return 2;
+  if (st.T < 200.0 || st.T > 6000.0) return 3;
+  if (last) return 0;
+  if (st.it >= L.max_iters) return 1;
+  return -1;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = L.S, R = L.R;
+  double* s_sp = reinterpret_cast<double*>(smem_raw);
+  float4* s_rxf = reinterpret_cast<float4*>(s_sp + S * SP_STRIDE);
+  int4* s_ri = reinterpret_cast<int4*>(s_rxf + R);
+  float* s_spf = reinterpret_cast<float*>(s_ri + R);
+  float* s_tw = s_spf + S * SPF_STRIDE;
+  int* s_gptr = reinterpret_cast<int*>(s_tw + L.n_hi_bins * 2 * L.dft_n);
+  int* s_gent = s_gptr + S + 1;
+  for (int t = threadIdx.x; t < S * SP_STRIDE; t += blockDim.x) s_sp[t] = L.sp_tab[t];
+  for (int t = threadIdx.x; t < R; t += blockDim.x) s_rxf[t] = L.rx_tab_f[t];
+  for (int t = threadIdx.x; t < R; t += blockDim.x) s_ri[t] = L.rx_idx[t];
+  for (int t = threadIdx.x; t < S * SPF_STRIDE; t += blockDim.x) s_spf[t] = L.sp_tab_f[t];
+  for (int t = threadIdx.x; t < L.n_hi_bins * 2 * L.dft_n; t += blockDim.x) s_tw[t] = L.dft_tw_f[t];
+  for (int t = threadIdx.x; t <= S; t += blockDim.x) s_gptr[t] = L.g_ptr[t];
+  for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
+  __syncthreads();
+  const TablesF tb{s_sp, s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw};
+
+  const int group = threadIdx.x / G;
+  const int l = threadIdx.x % G;
+  const size_t tables = table_smem_bytes_mixed(S, R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, R, L.Rrev, L.dft_n);
+  unsigned char* base = smem_raw + tables + (size_t)group * cell_bytes;
+  double* cY = reinterpret_cast<double*>(base);
+  double* cG2 = cY + S;
+  float* cC = reinterpret_cast<float*>(cG2 + S);
+  float* cH = cC + S;
+  float* cQ = cH + S;
+  float* cHist = cQ + R;
+  float* cRof = cHist + L.dft_n * L.Rrev;
+  for (int i = l; i < S; i += G) cY[i] = 0.0;
+
+  const unsigned long long n = (unsigned long long)L.n_cells;
+  CellState st;
+  st.cell = -1;
+  st.T = 1000.0;
+  st.P = kPatm;
+  st.t_rem = 1.0;
+  st.it = 0;
+  st.nhist = 0;
+  bool exhausted = false;
+  while (true) {
+    const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
+    if (c >= 0) {
+      st.cell = c;
+      st.T = L.T[c];
+      st.P = L.P[c];
+      st.t_rem = L.dt;
+      st.it = 0;
+      st.nhist = 0;
+      if (L.y_soa)
+        for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
+      else
+        for (int i = l; i < S; i += G) cY[i] = L.Y[c * S + i];
+      for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0f;
+    }
+    __syncwarp();
+    if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
+    const int outcome = step_mixed<G>(L, tb, cY, cG2, cC, cH, cQ, cHist, cRof, l, st);
+    if (st.cell >= 0 && outcome >= 0) {
+      const long long c = st.cell;
+      if (l == 0) {
+        L.T_out[c] = st.T;
+        L.iters[c] = st.it;
+        L.status[c] = (unsigned char)outcome;
+      }
+      if (L.y_soa)
+        for (int i = l; i < S; i += G) L.Y_out[(long long)i * L.n_cells + c] = cY[i];
+      else
+        for (int i = l; i < S; i += G) L.Y_out[c * S + i] = cY[i];
+      st.cell = -1;
+    }
+  }
+}
+
+}  // namespace stev

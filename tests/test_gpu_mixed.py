@@ -1,0 +1,92 @@
+"""Error of the mixed-precision CUDA path against the FP64 CPU oracle.
+
+The mixed path evaluates rates, the limiter and the ringing test in FP32 and
+keeps FP64 for Y, T and the Gibbs exponent of K.  Its target is
+max|dY| <= 1e-4 and |dT| <= 0.5 K.  As for the FP64 path (test_gpu_fp64),
+STEV's final state is ill-conditioned on ringing cells, so the target is
+required on every cell that the oracle's single-precision-sized conditioning
+probe (kf changed by 2^-22, K by 2^-18) leaves within 1e-6 / 1e-3 K, and the
+rest must stay within the validity bounds of test_gpu_fp64 (twice the
+limiter's per-step bound, the first-order enthalpy drift)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_09395_b300 import MIXED, Mechanism, synth
+from test_gpu_fp64 import _enthalpy
+
+pytestmark = pytest.mark.gpu
+
+TOL_Y, TOL_T = 1e-4, 0.5
+WELL_Y, WELL_T = 1e-6, 1e-3
+
+
+def _solve(mech, T, P, Y, dt, **opts):
+    import torch
+    m = Mechanism(mech, precision=MIXED, **opts)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (T, P, Y)]
+    out = tuple(x.cpu().numpy() for x in m.solve(*d, dt))
+    m.close()
+    return out
+
+
+def _check(mech, T0, Y0, gpu, ref, sY, sT, label):
+    To, Yo, it, st = gpu
+    rT, rY, rit, rst = ref
+    assert (st == rst).all(), "status differs in %d cells" % int((st != rst).sum())
+    dY = np.abs(Yo - rY).max(axis=1)
+    dT = np.abs(To - rT)
+    well = (sY < WELL_Y) & (sT < WELL_T)
+    bad = np.nonzero(well & ((dY > TOL_Y) | (dT > TOL_T)))[0]
+    assert bad.size == 0, "well-conditioned cells over target: %s dY %s dT %s" % (
+        bad[:8], dY[bad[:8]], dT[bad[:8]])
+    assert np.all(dY <= np.maximum(TOL_Y + 100 * sY, 2e-3)), "Y beyond validity bound"
+    H0, _, _ = _enthalpy(mech, T0, Y0)
+    Hg, cpg, hWg = _enthalpy(mech, To, Yo)
+    Ho, _, _ = _enthalpy(mech, rT, rY)
+    limT = TOL_T + 100 * sT + (np.abs(Hg - H0) + np.abs(Ho - H0) +
+                               np.sum(np.abs(Yo - rY) * np.abs(hWg), axis=1)) / cpg
+    assert np.all(dT <= limT), "T beyond validity bound"
+    np.testing.assert_allclose(Yo.sum(axis=1), Y0.sum(axis=1), rtol=0, atol=1e-9)
+    within = np.mean((dY <= TOL_Y) & (dT <= TOL_T))
+    print("%s: well-conditioned %.3f, within target %.4f, max dY %.3g (well %.3g), max dT %.3g,"
+          " iteration match %.3f" % (label, well.mean(), within, dY.max(),
+                                     dY[well].max() if well.any() else 0, dT.max(),
+                                     np.mean(it == rit)))
+    return within
+
+
+def test_mixed_small_case():
+    mech, T, P, Y, dt = synth.small_case(4096)
+    ref, sY, sT = oracle.conditioning(mech, T, P, Y, dt, level="fp32")
+    within = _check(mech, T, Y, _solve(mech, T, P, Y, dt), ref, sY, sT, "mixed 8/20 x 4096")
+    assert within > 0.8
+
+
+def test_mixed_scale_mechanism():
+    mech = synth.scale_mechanism()
+    T, P, Y = synth.make_cells(mech, 192, seed=11, T_range=(800, 2200), P_atm_range=(1, 5),
+                               dirichlet=0.5)
+    ref, sY, sT = oracle.conditioning(mech, T, P, Y, 1e-3, level="fp32")
+    _check(mech, T, Y, _solve(mech, T, P, Y, 1e-3), ref, sY, sT, "mixed 32/150 x 192")
+
+
+@pytest.mark.parametrize("k", [1, 14, 50])
+def test_mixed_prefix(k):
+    # a few steps in: single-precision rates move the state by ~1e-7 per unit
+    mech, T, P, Y, dt = synth.small_case(2048)
+    ref = oracle.solve(mech, T, P, Y, dt, max_iters=k)
+    To, Yo, it, st = _solve(mech, T, P, Y, dt, max_iters=k)
+    assert (it == ref[2]).all() and (st == ref[3]).all()
+    assert np.abs(Yo - ref[1]).max() <= 1e-5
+    assert np.abs(To - ref[0]).max() <= 1e-2
+
+
+def test_mixed_large_mechanism_prefix():
+    mech = synth.large_mechanism()
+    T, P, Y = synth.make_cells(mech, 64, seed=12, T_range=(700, 2500), P_atm_range=(1, 5),
+                               dirichlet=0.5)
+    ref = oracle.solve(mech, T, P, Y, 5e-4, max_iters=20)
+    To, Yo, it, st = _solve(mech, T, P, Y, 5e-4, max_iters=20)
+    assert (it == ref[2]).all()
+    assert np.abs(Yo - ref[1]).max() <= 1e-5
