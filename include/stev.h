@@ -15,8 +15,8 @@
  *     tables passed to stev_mechanism_create are HOST pointers, copied.
  *   - Calls are asynchronous on `cuda_stream` (NULL = legacy default stream)
  *     unless stated otherwise; completion is observed through the stream.
- *   - A mechanism owns its device tables and its per-slot solver state; at
- *     most one solve may be in flight per mechanism at a time.
+ *   - A mechanism owns its device tables and a work counter; at most one
+ *     solve may be in flight per mechanism at a time.
  *   - Errors are returned as stev_status; stev_last_error() gives a message
  *     (thread-local).  Per-cell outcomes go to the cell_status array.
  */
@@ -68,6 +68,8 @@ typedef struct {
   int precision;      /* STEV_FP64 or STEV_MIXED */
   int thermo;         /* STEV_THERMO_POLY or STEV_THERMO_MLP */
   int dft_on;         /* 0 disables the Sec. 2.3 damper (1) */
+  int lanes_per_cell; /* lanes that share one cell: 8, 16 or 32; 0 = chosen per
+                         mechanism and precision (0) */
 } stev_options;
 
 /* Fills *opt with the defaults above.  Never fails for a non-NULL opt. */
@@ -118,7 +120,9 @@ stev_status stev_solve(stev_mechanism *mech, long n_cells, const double *T, cons
                        int *iters, unsigned char *cell_status, void *cuda_stream);
 
 /* As stev_solve, but Y and Y_out are species-major [S][n_cells] (structure of
- * arrays), the layout the solver works in; no transposes are made. */
+ * arrays), for callers that keep their state that way.  The solver stages a
+ * whole cell per lane group, so its loads here are strided by n_cells; the
+ * cell-major layout of stev_solve is the coalesced one. */
 stev_status stev_solve_soa(stev_mechanism *mech, long n_cells, const double *T, const double *P,
                            const double *Y_soa, double dt_cfd, double *T_out, double *Y_out_soa,
                            int *iters, unsigned char *cell_status, void *cuda_stream);

@@ -70,9 +70,16 @@ PROBES = {"kf_up": ["-DORACLE_KF_SCALE=(1.0+2.220446049250313e-16)"],
           "kf32_up": ["-DORACLE_KF_SCALE=(1.0+2.384185791015625e-07)"],
           "kf32_down": ["-DORACLE_KF_SCALE=(1.0-2.384185791015625e-07)"],
           "K32_up": ["-DORACLE_K_SCALE=(1.0+3.814697265625e-06)"],
-          "K32_down": ["-DORACLE_K_SCALE=(1.0-3.814697265625e-06)"]}
+          "K32_down": ["-DORACLE_K_SCALE=(1.0-3.814697265625e-06)"],
+          # concentrations or net rates rounded to float every step
+          "round32_C": ["-DORACLE_ROUND32_C"],
+          "round32_q": ["-DORACLE_ROUND32_Q"]}
 PROBE_LEVELS = {"fp64": ("kf_up", "kf_down", "K_up", "K_down"),
-                "fp32": ("kf32_up", "kf32_down", "K32_up", "K32_down")}
+                "fp32": ("kf32_up", "kf32_down", "K32_up", "K32_down", "round32_C",
+                         "round32_q")}
+# single-precision-sized changes of the thresholds that take discrete
+# decisions (the limiter's Y_step^max, the ringing tolerances of Eq. 12)
+OPTION_PROBES = {"fp64": (), "fp32": ("y_step_max", "tol_freq", "tol_ring")}
 
 
 def _lib_path(probe: Optional[str]) -> str:
@@ -254,14 +261,22 @@ def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] =
     |change| of Y (over species) and of T between the default build and the
     probe builds of the given level: "fp64" changes every kf by one ulp and
     every K by 64 ulp; "fp32" by 2^-22 and 2^-18, the size of the rounding
-    of a single-precision rate and of its exponent.  A cell whose spread is far below a tolerance is
+    of a single-precision rate and of its exponent, rounds every
+    concentration or every net rate to float, and moves the limiter's
+    Y_step^max and the ringing tolerances by 2^-22.  A cell whose spread is far below a tolerance is
     well-conditioned at that tolerance."""
     if base is None:
         base = solve(mech, T, P, Y, dt, n_threads=n_threads, **opts)
     dY = np.zeros(len(T))
     dT = np.zeros(len(T))
-    for p in PROBE_LEVELS[level]:
-        r = solve(mech, T, P, Y, dt, n_threads=n_threads, probe=p, **opts)
+    runs = [dict(probe=p) for p in PROBE_LEVELS[level]]
+    for name in OPTION_PROBES[level]:
+        v = opts.get(name, DEFAULT_OPTS[name])
+        runs += [{name: v * (1.0 + 2.0 ** -22)}, {name: v * (1.0 - 2.0 ** -22)}]
+    for extra in runs:
+        kw = dict(opts)
+        kw.update(extra)
+        r = solve(mech, T, P, Y, dt, n_threads=n_threads, **kw)
         dY = np.maximum(dY, np.abs(r[1] - base[1]).max(axis=1))
         dT = np.maximum(dT, np.abs(r[0] - base[0]))
     return base, dY, dT

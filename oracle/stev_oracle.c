@@ -46,7 +46,7 @@
 #define ORACLE_PATM 101325.0       /* Pa, the 1 atm of Eq. 30 */
 #define ORACLE_PI 3.14159265358979323846
 
-/* Conditioning probe: the test suite also builds this file with kf scaled by
+/* Conditioning probes: the test suite also builds this file with kf scaled by
  * 1 +- 1 ulp, or K scaled by 1 +- 64 ulp (the rounding error of dG/RT, a sum
  * of terms up to ~64 in size, is of that order), to measure how far a cell's
  * result moves under a rounding-size change of its rates.  The default build
@@ -56,6 +56,18 @@
 #endif
 #ifndef ORACLE_K_SCALE
 #define ORACLE_K_SCALE 1.0
+#endif
+/* Single-precision probes: round every concentration (ORACLE_ROUND32_C) or
+ * every net rate of progress (ORACLE_ROUND32_Q) to the nearest float. */
+#ifdef ORACLE_ROUND32_C
+#define ORACLE_C(x) ((double)(float)(x))
+#else
+#define ORACLE_C(x) (x)
+#endif
+#ifdef ORACLE_ROUND32_Q
+#define ORACLE_Q(x) ((double)(float)(x))
+#else
+#define ORACLE_Q(x) (x)
 #endif
 
 typedef struct {
@@ -136,7 +148,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
   for (int i = 0; i < S; ++i) {
     double y = Y[i] > 0.0 ? Y[i] : 0.0;
     double ystar2 = (o->alpha > 0.0) ? y * (y / (o->alpha + y)) : y;
-    C[i] = rho * ystar2 / m->mol_weight[i];
+    C[i] = ORACLE_C(rho * ystar2 / m->mol_weight[i]);
   }
 
   /* Eqs. 29-30: kf = A T^beta exp(-Ea/RT);
@@ -163,7 +175,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
         if (nu > 0.0) rev *= int_power(C[m->rxn_species[k]], nu);
       }
     }
-    q[r] = fwd - rev;
+    q[r] = ORACLE_Q(fwd - rev);
   }
 
   /* Eq. 14 effective rates, production rates in ascending reaction order */

@@ -43,6 +43,7 @@ class Options(ctypes.Structure):
         ("tol_ring", ctypes.c_double), ("tol_freq", ctypes.c_double),
         ("r_fac", ctypes.c_double), ("rof_min", ctypes.c_double), ("max_iters", ctypes.c_int),
         ("precision", ctypes.c_int), ("thermo", ctypes.c_int), ("dft_on", ctypes.c_int),
+        ("lanes_per_cell", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -82,6 +82,7 @@ extern "C" void stev_default_options(stev_options* o) {
   o->precision = STEV_FP64;
   o->thermo = STEV_THERMO_POLY;
   o->dft_on = 1;
+  o->lanes_per_cell = 0;
 }
 
 static stev_status check_options(const stev_options* o) {
@@ -98,6 +99,9 @@ static stev_status check_options(const stev_options* o) {
   if (o->max_iters < 1) return fail(STEV_EINVAL, "max_iters must be >= 1");
   if (o->precision != STEV_FP64 && o->precision != STEV_MIXED) return fail(STEV_EINVAL, "unknown precision");
   if (o->thermo != STEV_THERMO_POLY && o->thermo != STEV_THERMO_MLP) return fail(STEV_EINVAL, "unknown thermo mode");
+  if (o->lanes_per_cell != 0 && o->lanes_per_cell != 8 && o->lanes_per_cell != 16 &&
+      o->lanes_per_cell != 32)
+    return fail(STEV_EINVAL, "lanes_per_cell must be 0, 8, 16 or 32");
   if (o->thermo == STEV_THERMO_MLP)
     return fail(STEV_EINVAL, "thermo mode not available in this build");
   return STEV_OK;
@@ -129,9 +133,12 @@ static KernelFn select_kernel(int precision, int G) {
   }
 }
 
-// Lanes per cell: enough to cover the species and most reactions in one or
-// two rounds without leaving most lanes idle on small mechanisms.
-static int choose_group(int S, int R) {
+// Lanes per cell.  Per-cell scalar work (log T, 1/T, h, t_rem) is one warp
+// instruction whatever the group size, so more cells per warp amortise it;
+// fewer lanes per cell lengthen each cell's step (the tail of the variable
+// load).  FP64: cover the species and most reactions in one or two rounds.
+static int choose_group(int S, int R, const stev_options& o) {
+  if (o.lanes_per_cell) return o.lanes_per_cell;
   if (S <= 8 && R <= 32) return 8;
   if (S <= 16 && R <= 64) return 16;
   return 32;
@@ -143,7 +150,7 @@ static int choose_group(int S, int R) {
 static stev_status configure(stev_mechanism* m) {
   cudaDeviceProp prop;
   CUDA_TRY(cudaGetDeviceProperties(&prop, m->device));
-  m->G = choose_group(m->S, m->R);
+  m->G = choose_group(m->S, m->R, m->opt);
   const int G = m->G;
   const bool mixed = m->opt.precision == STEV_MIXED;
   const size_t tables =

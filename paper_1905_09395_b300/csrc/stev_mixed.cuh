@@ -3,10 +3,14 @@
 // Same structure as the FP64 kernel (a group of G lanes per cell, all cell
 // state in shared memory, species-major gather, ballot/popcount refill).
 // What changes is the arithmetic:
-//   FP64  Y and T (the forward Euler update of Eq. 18), t_rem and h, G/RT of
-//         every species and the per-reaction Gibbs difference
-//         dG/RT - dN ln(P_atm/RT) that sets K (Eq. 30), whose cancellation of
-//         large terms is where precision matters;
+//   FP64  Y and T (the forward Euler update of Eq. 18), t_rem and h, and G/RT
+//         of every species;
+//   FP64-grade, on the FP32 pipe: the per-reaction Gibbs difference
+//         dG/RT - dN ln(P_atm/RT) that sets K (Eq. 30).  It is where large
+//         terms cancel, so each species' FP64 value is split into an exact
+//         float pair hi + lo and the difference is summed with error-free
+//         transformations (Knuth's TwoSum), keeping >= 48 significant bits
+//         before the single rounding to FP32 that the exponential takes;
 //   FP32  mixture, cp/R and H/RT (Eqs. 15-16), gamma and concentrations
 //         (Eqs. 6-7), forward and reverse rate constants (exponentials on the
 //         MUFU unit in base 2: k = 2^(log2 k)), rates of progress and rOF
@@ -25,6 +29,13 @@ __device__ __forceinline__ float ex2f(float x) {
   return r;
 }
 
+// Knuth's TwoSum: s + err == a + b exactly (round-to-nearest, no FMA needed).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 struct TablesF {
   const double* sp;   // double species table (G/RT coefficients)
   const float* spf;   // float species table
@@ -37,7 +48,7 @@ struct TablesF {
 
 template <int G>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
-                                          double* cG2, float* cC, float* cH, float* cQ,
+                                          float2* cG2, float* cC, float* cH, float* cQ,
                                           float* cHist, float* cRof, int l, CellState& st) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
@@ -67,7 +78,9 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
     cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
     const double gp = fma(fma(fma(bd[B_G4], T, bd[B_G3]), T, bd[B_G2]), T, bd[B_H1]);
-    cG2[i] = (fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T) * kLog2e;
+    const double g2 = (fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T) * kLog2e;
+    const float ghi = (float)g2;
+    cG2[i] = make_float2(ghi, (float)(g2 - (double)ghi));  // g2 == hi + lo to ~2^-48
     cpp = fmaf(Yi * cpR, spf[SPF_INVW], cpp);
     const float y = fmaxf(Yi, 0.0f);
     const float ys = (L.alpha > 0.0) ? y * __fdividef(y, (float)L.alpha + y) : y;
@@ -77,8 +90,10 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   __syncwarp();
 
   // rates of progress: kf = 2^(lg2 A + beta lg2 T - Ea/R log2e / T) (FP32);
-  // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e formed in FP64
+  // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e summed exactly
   const double lg2Pref = (L.ln_patm_over_ru - lnT) * kLog2e;
+  const float prefHi = (float)lg2Pref;
+  const float prefLo = (float)(lg2Pref - (double)prefHi);
   const int ktap = st.nhist % N;
   for (int r = l; r < R; r += G) {
     const float4 rx = tb.rxf[r];
@@ -90,10 +105,27 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     if (a1 != kNone) q *= cC[a1];
     float rof = 1.0f;
     if (ri.z) {
-      double dG = cG2[p0] - cG2[a0];
-      if (a1 != kNone) dG -= cG2[a1];
-      if (p1 != kNone) dG += cG2[p1];
-      const float x = (float)fma(-(double)rx.w, lg2Pref, dG);
+      // x = sum nu g2 - dN lg2Pref as a float pair (s, e): TwoSum on the
+      // high parts, plain sums of the error terms and low parts
+      const float2 gp0 = cG2[p0], ga0 = cG2[a0];
+      float sx, e, t;
+      two_sum(gp0.x, -ga0.x, sx, t);
+      e = t + (gp0.y - ga0.y);
+      if (a1 != kNone) {
+        const float2 g = cG2[a1];
+        two_sum(sx, -g.x, sx, t);
+        e += t - g.y;
+      }
+      if (p1 != kNone) {
+        const float2 g = cG2[p1];
+        two_sum(sx, g.x, sx, t);
+        e += t + g.y;
+      }
+      if (rx.w != 0.0f) {  // dN in {-1, 1}: exact scaling of the pair
+        two_sum(sx, -rx.w * prefHi, sx, t);
+        e += t - rx.w * prefLo;
+      }
+      const float x = sx + e;
       float rev = ex2f(lg2kf + x) * cC[p0];
       if (p1 != kNone) rev *= cC[p1];
       q -= rev;
@@ -222,7 +254,7 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
   const size_t cell_bytes = cell_smem_bytes_mixed(S, R, L.Rrev, L.dft_n);
   unsigned char* base = smem_raw + tables + (size_t)group * cell_bytes;
   double* cY = reinterpret_cast<double*>(base);
-  double* cG2 = cY + S;
+  float2* cG2 = reinterpret_cast<float2*>(cY + S);
   float* cC = reinterpret_cast<float*>(cG2 + S);
   float* cH = cC + S;
   float* cQ = cH + S;
