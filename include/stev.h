@@ -134,6 +134,30 @@ stev_status stev_solve_host(stev_mechanism *mech, long n_cells, const double *T,
                             const double *Y, double dt_cfd, double *T_out, double *Y_out,
                             int *iters, unsigned char *cell_status, void *cuda_stream);
 
+/* As stev_solve_host, but allocates nothing.  For callers that may not allocate
+ * device memory when they solve: a CFD code whose device memory belongs to its
+ * own pool allocator and budget, a real-time or callback context where
+ * cudaMalloc's implicit synchronisation is not acceptable, or a process that
+ * must not grow its device footprint after start-up.  (The paper has no
+ * counterpart; it is a property of this library's interface.)
+ *   Staging goes through one fixed 16 MiB device array in the library, shared
+ *   by every call and held by every GPU that loads the library until exit.
+ *   A call needs  256 + align(8n)*2 + align(8nS) + align(8n) + align(8nS)
+ *   + align(4n) + align(n)  bytes (align = round up to 256); larger n_cells
+ *   are rejected with STEV_EINVAL and a message giving the largest n that
+ *   fits (about 31,000 cells at S = 32).
+ *   The first call on a device looks up the array's device address (a one-off
+ *   set-up); make that first call before any stream capture.
+ *   The array keeps the previous call's contents; the work counter is cleared
+ *   on every call.  Calls whose GPU work overlaps (different streams, host
+ *   threads) race on the array: serialise them.
+ *   No cudaMalloc, cudaFree or other allocating routine is called.  Blocks
+ *   until the results are in the host arrays. */
+stev_status stev_solve_host_noalloc(stev_mechanism *mech, long n_cells, const double *T,
+                                    const double *P, const double *Y, double dt_cfd,
+                                    double *T_out, double *Y_out, int *iters,
+                                    unsigned char *cell_status, void *cuda_stream);
+
 /* Number of resident solver slots (cells in flight) of the persistent kernel
  * on the current device for this mechanism and its options. */
 long stev_resident_slots(const stev_mechanism *mech);

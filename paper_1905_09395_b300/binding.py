@@ -26,7 +26,7 @@ THERMO_POLY, THERMO_MLP = 0, 1
 EXPORTS = (
     "stev_default_options", "stev_mechanism_create", "stev_mechanism_set_options",
     "stev_mechanism_get_options", "stev_solve", "stev_solve_soa", "stev_solve_host",
-    "stev_resident_slots", "stev_destroy", "stev_last_error",
+    "stev_resident_slots", "stev_destroy", "stev_last_error", "stev_solve_host_noalloc",
 )
 
 
@@ -70,7 +70,7 @@ def lib():
         L.stev_mechanism_set_options.restype = I
         L.stev_mechanism_get_options.argtypes = [P, P]
         L.stev_mechanism_get_options.restype = I
-        for name in ("stev_solve", "stev_solve_soa", "stev_solve_host"):
+        for name in ("stev_solve", "stev_solve_soa", "stev_solve_host", "stev_solve_host_noalloc"):
             f = getattr(L, name)
             f.argtypes = [P, LNG, P, P, P, D, P, P, P, P, P]
             f.restype = I

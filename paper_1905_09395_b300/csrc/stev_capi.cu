@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -502,3 +503,100 @@ extern "C" void stev_destroy(stev_mechanism* m) {
 }
 
 extern "C" const char* stev_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------ solve without allocating
+// Some callers may not allocate device memory at solve time: a CFD code whose
+// device memory is owned by its own pool allocator and budget, a real-time or
+// host-callback context where cudaMalloc's implicit device synchronisation is
+// not acceptable, or a process that must not grow its footprint after start-up.
+// stev_solve_host_noalloc serves them: it stages the host arrays through one
+// file-scope device array of fixed size instead of mechanism-owned buffers,
+// and calls no cudaMalloc, cudaFree or other allocating routine.
+//
+// Layout of the array for n cells of S species, each piece 256-byte aligned:
+// [work counter][T][P][Y n*S][T_out][Y_out n*S][iters][status].
+static constexpr size_t kNoAllocBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_ptr[kNoAllocMaxDevices];  // device address per device, set once
+static std::mutex g_noalloc_mutex;
+
+static size_t noalloc_align(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t noalloc_bytes(long n, int S) {
+  const size_t nn = (size_t)n;
+  return noalloc_align(sizeof(unsigned long long)) + 2 * noalloc_align(nn * 8) +
+         noalloc_align(nn * S * 8) + noalloc_align(nn * 8) + noalloc_align(nn * S * 8) +
+         noalloc_align(nn * 4) + noalloc_align(nn);
+}
+
+extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const double* T,
+                                               const double* P, const double* Y, double dt,
+                                               double* T_out, double* Y_out, int* iters,
+                                               unsigned char* cell_status, void* stream) {
+  g_err.clear();
+  if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (n < 0) return fail(STEV_EINVAL, "n_cells < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(STEV_EINVAL, "dt_cfd must be finite and > 0");
+  if (n == 0) return STEV_OK;
+  if (!T || !P || !Y || !T_out || !Y_out || !iters || !cell_status)
+    return fail(STEV_EINVAL, "NULL array");
+  if (noalloc_bytes(n, m->S) > kNoAllocBytes) {
+    long lo = 0, hi = n;  // noalloc_bytes(lo) fits, noalloc_bytes(hi) does not
+    while (hi - lo > 1) {
+      const long mid = (lo + hi) / 2;
+      if (noalloc_bytes(mid, m->S) <= kNoAllocBytes) lo = mid; else hi = mid;
+    }
+    return fail(STEV_EINVAL,
+                "stev_solve_host_noalloc: %ld cells of %d species need %zu bytes of staging; "
+                "its fixed device array holds %zu bytes (at most %ld cells)",
+                n, m->S, noalloc_bytes(n, m->S), kNoAllocBytes, lo);
+  }
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(STEV_EINVAL, "mechanism lives on device %d, current is %d", m->device, dev);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(STEV_EINVAL, "device index %d out of range", dev);
+  unsigned char* base = nullptr;
+  {
+    // set-up, once per device: the array's device address (host code only
+    // knows a stand-in for it)
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = p;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+  const size_t nn = (size_t)n;
+  unsigned char* q = base;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(q);
+  q += noalloc_align(sizeof(unsigned long long));
+  double* dT = reinterpret_cast<double*>(q);   q += noalloc_align(nn * 8);
+  double* dP = reinterpret_cast<double*>(q);   q += noalloc_align(nn * 8);
+  double* dY = reinterpret_cast<double*>(q);   q += noalloc_align(nn * m->S * 8);
+  double* dTo = reinterpret_cast<double*>(q);  q += noalloc_align(nn * 8);
+  double* dYo = reinterpret_cast<double*>(q);  q += noalloc_align(nn * m->S * 8);
+  int* dit = reinterpret_cast<int*>(q);        q += noalloc_align(nn * 4);
+  unsigned char* dst = q;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(dT, T, nn * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dP, P, nn * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dY, Y, nn * m->S * 8, cudaMemcpyHostToDevice, s));
+  // the counter must start at zero; it keeps the previous call's value
+  CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  Launch L = make_launch(m, n, dt);
+  L.T = dT; L.P = dP; L.Y = dY;
+  L.T_out = dTo; L.Y_out = dYo; L.iters = dit; L.status = dst;
+  L.y_soa = 0;
+  L.counter = counter;
+  select_kernel(m->opt.precision, m->G)<<<m->grid, m->block, m->smem, s>>>(L);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(T_out, dTo, nn * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(Y_out, dYo, nn * m->S * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(iters, dit, nn * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(cell_status, dst, nn, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return STEV_OK;
+}
