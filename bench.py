@@ -2,11 +2,14 @@
 
 One step = one stev_solve of every cell of the workload (32 species / 150
 reactions, T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), dt = 1e-3 s),
-i.e. one pass of the whole hot path over one batch.  Cells are independent,
+i.e. one pass of the whole hot path over one batch.  The line's value is the
+mixed-precision path; the plain FP64 path is timed once on the same cells
+beside it ("plain_fp64").  Warm-up solves run the same kernel and launch
+configuration on the first --warmup-cells cells.  Cells are independent,
 so with N GPUs every rank solves its own batch (weak scaling, no collective on
 the data path; a barrier only brackets the timed region).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
     python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
 
 Smaller cases for profiling: --cells N and --max-iters K shrink the workload
@@ -37,6 +40,11 @@ N_CELLS = 1 << 20
 EXP_OPS, LOG_OPS, DIV_OPS = 16.0, 30.0, 7.5
 # FP64 pipe peak: 1.667 DFMA/clk/SM x 148 SMs at the probe's 1919 MHz under load
 FP64_PEAK_OPS = 4.733e11
+# DRAM bytes per cell of one launch, from the ncu captures summarised in
+# profiles/ (3,108- and 1,628-cell cases; reads only: the small cases' output
+# writes stay in L2), scaled to the full launch by the cells it processes.
+# Set to None when the kernel changes after the capture.
+DRAM_BYTES_PER_CELL = {"mixed": 924160 / 3108, "fp64": 528896 / 1628}
 
 
 def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
@@ -57,6 +65,15 @@ def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
     dft = Rrev * (1 + 12 + 3)
     scalars = 12 + LOG_OPS + 3 * DIV_OPS
     return species + reactions + gather + dft + scalars
+
+
+def mixed_fp64_ops_per_cell_step(S: int) -> float:
+    """FP64 work the mixed-precision plan itself requires per cell-step, in
+    DFMA-equivalents: per species G/RT (7) and its split into a float pair (2)
+    and the FP64 Euler update with its conversion (2); per cell log T, 1/T and
+    the h / t_rem / T bookkeeping (~10).  Everything else runs on the FP32 and
+    MUFU pipes, which have 64x and 16x the FP64 pipe's rate."""
+    return S * (7 + 2 + 2) + LOG_OPS + DIV_OPS + 10
 
 
 def workload(n_cells: int, rank: int = 0):
@@ -181,6 +198,32 @@ def run_reference(args):
     return 0
 
 
+def timed_solves(m, Td, Pd, Yd, dt, out, steps, warmup, warmup_cells, stream, dist=None,
+                 sample_clocks=None):
+    """W warm-up solves on the first warmup_cells cells (same kernel and launch
+    configuration), then K timed solves of every cell, CUDA events on the
+    launching stream, synchronised and barriered on both sides."""
+    import torch
+    nw = min(Td.shape[0], warmup_cells)
+    wout = tuple(x[:nw] for x in out)
+    for _ in range(warmup):
+        m.solve(Td[:nw], Pd[:nw], Yd[:nw], dt, out=wout)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for k in range(steps):
+        ev[k][0].record(stream)
+        m.solve(Td, Pd, Yd, dt, out=out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    barrier(dist)
+    return [a.elapsed_time(b) for a, b in ev], wall, nw
+
+
 def run_ours(args):
     import torch
     from paper_1905_09395_b300 import Mechanism, binding
@@ -190,45 +233,25 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     mech, T, P, Y, dt = workload(args.cells, rank)
-    S = mech.n_species
-    opts = dict(precision=binding.MIXED if args.precision == "mixed" else binding.FP64)
-    if args.max_iters is not None:
-        opts["max_iters"] = args.max_iters
-    m = Mechanism(mech, **opts)
+    S, R = mech.n_species, mech.n_reactions
+    Rrev, nnz = int(mech.reversible.sum()), len(mech.rxn_species)
+    extra = {} if args.max_iters is None else {"max_iters": args.max_iters}
+    prec = binding.MIXED if args.precision == "mixed" else binding.FP64
+    m = Mechanism(mech, precision=prec, **extra)
     n = len(T)
     Td, Pd, Yd = (torch.from_numpy(a).to(dev) for a in (T, P, Y))
     out = (torch.empty_like(Td), torch.empty_like(Yd), torch.empty(n, dtype=torch.int32, device=dev),
            torch.empty(n, dtype=torch.uint8, device=dev))
     stream = torch.cuda.current_stream(dev)
 
-    # warm-up: the same kernel and launch configuration on the first slice
-    nw = min(n, args.warmup_cells)
-    wout = tuple(x[:nw] for x in out)
-    for _ in range(args.warmup):
-        m.solve(Td[:nw], Pd[:nw], Yd[:nw], dt, out=wout)
-    torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier(dist)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        t0 = time.time()
-        for k in range(args.steps):
-            ev[k][0].record(stream)
-            m.solve(Td, Pd, Yd, dt, out=out)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.time() - t0
-    barrier(dist)
-    ms = [a.elapsed_time(b) for a, b in ev]
+        ms, wall, nw = timed_solves(m, Td, Pd, Yd, dt, out, args.steps, args.warmup,
+                                    args.warmup_cells, stream, dist)
     dev_s = sum(ms) / 1e3
-    iters = out[2].to(torch.int64)
-    cell_steps = int(iters.sum().item())
-    status = torch.bincount(out[3].to(torch.int64), minlength=4).cpu().numpy()
     it_np = out[2].cpu().numpy()
+    cell_steps = int(it_np.astype(np.int64).sum())
+    status = np.bincount(out[3].cpu().numpy(), minlength=4)
 
-    # max over ranks
     t_max = dev_s
     total_cells = n * args.steps
     if dist is not None:
@@ -263,29 +286,61 @@ def run_ours(args):
         e2e = {"value": n * world * ke / el, "unit": UNIT,
                "h2d_bytes_per_step": int(hT.nbytes + hP.nbytes + hY.nbytes),
                "d2h_bytes_per_step": int(sum(x.nbytes for x in ho)), "steps": ke}
+    m.close()
+
+    # the plain FP64 path on the same cells, for the mixed-vs-FP64 comparison
+    plain = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        mf = Mechanism(mech, precision=binding.FP64, **extra)
+        msf, wallf, _ = timed_solves(mf, Td, Pd, Yd, dt, out, 1, args.warmup,
+                                     args.warmup_cells, stream, dist)
+        itf = out[2].cpu().numpy().astype(np.int64)
+        tf = msf[0] / 1e3
+        if dist is not None:
+            t = torch.tensor([tf], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tf = float(t.item())
+        opsf = fp64_ops_per_cell_step(S, R, Rrev, nnz)
+        achf = opsf * int(itf.sum()) / (msf[0] / 1e3)
+        plain = {"value": n * world / tf, "unit": UNIT, "ms_per_step": tf * 1e3, "steps": 1,
+                 "warmup": args.warmup, "cell_steps_per_s": int(itf.sum()) / tf,
+                 "roofline": {"bound": "alu", "achieved": 2 * achf / 1e12,
+                              "peak": 2 * FP64_PEAK_OPS / 1e12, "unit": "TFLOP/s",
+                              "frac": achf / FP64_PEAK_OPS, "traffic": None,
+                              "ops_per_cell_step": opsf}}
+        mf.close()
 
     if rank != 0:
         return 0
-    ops = fp64_ops_per_cell_step(S, mech.n_reactions, int(mech.reversible.sum()),
-                                 len(mech.rxn_species))
-    per_launch_ops = ops * cell_steps
-    achieved = per_launch_ops / (float(np.mean(ms)) / 1e3)
+    if args.precision == "mixed":
+        ops = mixed_fp64_ops_per_cell_step(S)
+        ops_note = ("FP64 work the mixed plan requires (species G/RT and split, FP64 Euler, "
+                    "log T, 1/T, step bookkeeping); FP32/MUFU work not counted")
+    else:
+        ops = fp64_ops_per_cell_step(S, R, Rrev, nnz)
+        ops_note = ("the method's FP64 work: exp = %g, log = %g, div = %g DFMA-equivalents, "
+                    "measured" % (EXP_OPS, LOG_OPS, DIV_OPS))
+    achieved = ops * cell_steps / (float(np.mean(ms)) / 1e3)
+    bpc = DRAM_BYTES_PER_CELL.get(args.precision)
     roofline = {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * FP64_PEAK_OPS / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
-                "pipe": "fp64 (DFMA = 2 flops; exp = %g, log = %g, div = %g DFMA-equivalents,"
-                        " measured)" % (EXP_OPS, LOG_OPS, DIV_OPS),
-                "ops_per_cell_step": ops, "cell_steps_per_launch": cell_steps,
-                "peak_source": "measured fp64 pipe rate, csrc/alu_peaks.cu"}
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_OPS,
+                "traffic": None if bpc is None else bpc * n,
+                "traffic_note": "DRAM bytes per launch scaled from the ncu capture in profiles/",
+                "pipe": "fp64 (DFMA = 2 flops); peak = measured DFMA rate of csrc/alu_peaks.cu "
+                        "(1.667/clk/SM x 148 SMs x 1919 MHz)",
+                "ops_per_cell_step": ops, "ops_counted": ops_note,
+                "cell_steps_per_launch": cell_steps}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "syn32x150 (32 species, 150 reversible reactions), %d cells, "
-                                   "T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), dt 1e-3 s"
-                                   % n,
-                       "precision": args.precision, "cells_per_gpu": n,
-                       "warmup_cells": nw, "max_iters": m.options.max_iters,
+            "config": {"workload": "syn32x150 (32 species, 150 reversible reactions), %d cells "
+                                   "per GPU, T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), "
+                                   "dt 1e-3 s" % n,
+                       "precision": args.precision, "thermo": "NASA-7 polynomial",
+                       "cells_per_gpu": n, "warmup_cells": nw, "max_iters": extra.get(
+                           "max_iters", 200000),
                        "l2": "inputs (%d MB) larger than L2" % ((T.nbytes + P.nbytes + Y.nbytes)
                                                                 >> 20),
                        "parallelism": "dp%d (independent cell batches)" % world},
@@ -295,23 +350,23 @@ def run_ours(args):
             "cell_status": {"ok": int(status[0]), "maxiter": int(status[1]),
                             "nonfinite": int(status[2]), "trange": int(status[3])},
             "roofline": roofline, "gpu_launches": args.steps, "e2e": e2e,
-            "wall_s_timed": wall}
+            "plain_fp64": plain, "wall_s_timed": wall}
     line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu_baseline:
-        o = {} if args.max_iters is None else {"max_iters": args.max_iters}
-        line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **o)
+        line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **extra)
     print(json.dumps(line))
-    m.close()
     return 0
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain FP64 solve of the same cells (mixed runs only)")
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--warmup-cells", type=int, default=16384)
     ap.add_argument("--max-iters", type=int, default=None)
