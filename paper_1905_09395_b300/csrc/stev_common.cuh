@@ -40,6 +40,7 @@ struct CellState {
   double T, P, t_rem;
   int it;
   int nhist;
+  double lnT;       // mixed kernel: ln T kept up to date incrementally
 };
 
 struct Tables {

@@ -101,10 +101,11 @@ __host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gat
   return (b + 15) & ~(size_t)15;
 }
 
-// Mixed kernel cell: Y and G/RT log2 e in FP64 (S each); C, H/RT (S each),
-// rates (R), history [N][Rrev] and rOF (Rrev) in FP32.
+// Mixed kernel cell: Y in FP64 and G/RT log2 e as a float pair (8 bytes each
+// per species); C, H/RT, a float copy of Y (S each), rates (R), history
+// [N][Rrev] and rOF (Rrev) in FP32.
 __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n) {
-  size_t b = (size_t)16 * S + ((size_t)2 * S + R + (size_t)dft_n * Rrev + Rrev) * 4;
+  size_t b = (size_t)16 * S + ((size_t)3 * S + R + (size_t)dft_n * Rrev + Rrev) * 4;
   return (b + 15) & ~(size_t)15;
 }
 

@@ -46,23 +46,39 @@ struct TablesF {
   const float* tw;    // float twiddles
 };
 
+__device__ __forceinline__ float lg2f_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ln(1+u) for |u| <= 2^-10 from its series to u^5 (truncation < 2^-60 |u|)
+__device__ __forceinline__ double log1p_small(double u) {
+  double c = fma(u, 0.2, -0.25);
+  c = fma(c, u, 1.0 / 3.0);
+  c = fma(c, u, -0.5);
+  c = fma(c, u, 1.0);
+  return c * u;
+}
+
 template <int G>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
-                                          float2* cG2, float* cC, float* cH, float* cQ,
-                                          float* cHist, float* cRof, int l, CellState& st) {
+                                          float* cYf, float2* cG2, float* cC, float* cH,
+                                          float* cQ, float* cHist, float* cRof, float Pf, int l,
+                                          CellState& st) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
-  const double lnT = log(T);        // FP64: feeds G/RT
+  const double lnT = st.lnT;        // FP64: feeds G/RT
   const double invT = 1.0 / T;
   const float Tf = (float)T;
-  const float invTf = (float)invT;
-  const float lg2Tf = (float)(lnT * kLog2e);
+  const float invTf = 1.0f / Tf;
+  const float lg2Tf = lg2f_approx(Tf);
 
   // mixture (FP32)
   float part = 0.0f;
-  for (int i = l; i < S; i += G) part = fmaf((float)cY[i], tb.spf[i * SPF_STRIDE + SPF_INVW], part);
+  for (int i = l; i < S; i += G) part = fmaf(cYf[i], tb.spf[i * SPF_STRIDE + SPF_INVW], part);
   const float sumYW = group_sum<G>(part);
-  const float rho = (float)st.P / ((float)kRu * Tf * sumYW);
+  const float rho = Pf / ((float)kRu * Tf * sumYW);
 
   // thermo: cp/R, H/RT in FP32; G/RT in FP64 (in log2 units, G/RT * log2 e)
   float cpp = 0.0f;
@@ -72,7 +88,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const bool lo = T < sp[SP_TSPLIT];
     const float* b = spf + (lo ? SPF_LOW : SPF_HIGH);
     const double* bd = sp + (lo ? SP_LOW : SP_HIGH);
-    const float Yi = (float)cY[i];
+    const float Yi = cYf[i];
     const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf, b[BF_A1]), Tf,
                            b[BF_A0]);
     const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
@@ -151,7 +167,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     hwp = fmaf(cH[i], wd, hwp);
     cC[i] = ri;
     const float rstar = fmaxf(-ri, 1.0e-30f);
-    const float Yi = (float)cY[i];
+    const float Yi = cYf[i];
     const float ystar = (Yi < 1.0e-20f) ? 1.0f : 0.9f * Yi;
     tmin = fminf(tmin, __fdividef(fminf((float)L.y_step_max, ystar), rstar));
   }
@@ -213,11 +229,20 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   for (int i = l; i < S; i += G) {
     const double y = fma(h, (double)cC[i], cY[i]);
     cY[i] = y;
+    cYf[i] = (float)y;
     bad = bad || !isfinite(y);
   }
   st.T = fma(h, (double)dTdt, T);
   st.t_rem -= h;
   st.it += 1;
+  // ln T for the next step: ln T' = ln T + ln(1 + u), u = (T' - T)/T, from the
+  // series while |u| <= 2^-10; the library log every 256 steps and on larger
+  // changes keeps the accumulated rounding below ~1e-13
+  const double u = (st.T - T) * invT;
+  if (fabs(u) <= 0x1p-10 && (st.it & 255) != 0)
+    st.lnT = lnT + log1p_small(u);
+  else
+    st.lnT = log(st.T);
   bad = group_any<G>(bad) || !isfinite(st.T);
   __syncwarp();
   if (bad) return 2;
@@ -257,10 +282,14 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
   float2* cG2 = reinterpret_cast<float2*>(cY + S);
   float* cC = reinterpret_cast<float*>(cG2 + S);
   float* cH = cC + S;
-  float* cQ = cH + S;
+  float* cYf = cH + S;  // float shadow of Y for the FP32 parts
+  float* cQ = cYf + S;
   float* cHist = cQ + R;
   float* cRof = cHist + L.dft_n * L.Rrev;
-  for (int i = l; i < S; i += G) cY[i] = 0.0;
+  for (int i = l; i < S; i += G) {
+    cY[i] = 0.0;
+    cYf[i] = 0.0f;
+  }
 
   const unsigned long long n = (unsigned long long)L.n_cells;
   CellState st;
@@ -270,6 +299,8 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
   st.t_rem = 1.0;
   st.it = 0;
   st.nhist = 0;
+  st.lnT = log(1000.0);
+  float Pf = (float)kPatm;
   bool exhausted = false;
   while (true) {
     const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
@@ -280,15 +311,18 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
       st.t_rem = L.dt;
       st.it = 0;
       st.nhist = 0;
+      st.lnT = log(st.T);
+      Pf = (float)st.P;
       if (L.y_soa)
         for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
       else
         for (int i = l; i < S; i += G) cY[i] = L.Y[c * S + i];
+      for (int i = l; i < S; i += G) cYf[i] = (float)cY[i];
       for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0f;
     }
     __syncwarp();
     if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
-    const int outcome = step_mixed<G>(L, tb, cY, cG2, cC, cH, cQ, cHist, cRof, l, st);
+    const int outcome = step_mixed<G>(L, tb, cY, cYf, cG2, cC, cH, cQ, cHist, cRof, Pf, l, st);
     if (st.cell >= 0 && outcome >= 0) {
       const long long c = st.cell;
       if (l == 0) {
