@@ -158,6 +158,46 @@ stev_status stev_solve_host_noalloc(stev_mechanism *mech, long n_cells, const do
                                     double *T_out, double *Y_out, int *iters,
                                     unsigned char *cell_status, void *cuda_stream);
 
+/* ---- thermo network (Sec. 3: a small neural network of temperature stands in
+ * for the NASA-7 species properties; Figs. 2-3).  The library's network is
+ * t = (T - 1650)/1350, a1 = tanh(W1 t + b1), a2 = tanh(W2 a1 + b2) (64 each),
+ * y = W3 a2 + b3 (3S standardised outputs: cp/R of every species, then H/RT,
+ * then S/R; value = y * std + mean).  Parameters are one flat float array:
+ * W1[64], b1[64], W2[64][64], b2[64], W3[3S][64], b3[3S] (rows = outputs). */
+
+/* Number of network parameters of this mechanism (64*64 + 67*3S + 192). */
+long stev_mlp_num_params(const stev_mechanism *mech);
+
+/* Trains the network on the GPU with the library's own kernels: targets are
+ * the NASA-7 polynomials at the given HOST temperatures (FP64, stored FP32,
+ * standardised per output), FP32 forward/backward, Adam (lr, beta 0.9/0.999)
+ * over minibatches of `batch` samples for `epochs` epochs, weights
+ * initialised Xavier-uniform from splitmix64(seed).  loss_per_epoch (host,
+ * nullable) receives each epoch's mean squared error in standardised units.
+ * Afterwards inference uses BF16 copies of W2, W3.  Synchronous. */
+stev_status stev_mlp_train(stev_mechanism *mech, const double *T_samples, long n_samples,
+                           int epochs, int batch, float lr, unsigned long long seed,
+                           float *loss_per_epoch);
+
+/* Sets / reads the network parameters (HOST arrays) and the per-output mean and
+ * standard deviation ([3S] each) used to undo the standardisation. */
+stev_status stev_mlp_set_params(stev_mechanism *mech, const float *params, long n_params,
+                                const float *mean, const float *stdv);
+stev_status stev_mlp_get_params(const stev_mechanism *mech, float *params, long n_params,
+                                float *mean, float *stdv);
+
+/* Mean-squared error of the network with parameters `params` on n samples
+ * (HOST: T [n], standardised targets [n][3S]) and its gradient (HOST,
+ * [n_params]), computed by the training kernel (FP32).  Synchronous. */
+stev_status stev_mlp_loss_grad(stev_mechanism *mech, const float *params, const double *T,
+                               const float *target, long n, float *grad, double *loss);
+
+/* Evaluates the trained network (BF16 tensor-core MMAs, FP32 accumulation) at
+ * n DEVICE temperatures; props (DEVICE) receives [n][3S] values (cp/R, H/RT,
+ * S/R).  Asynchronous on cuda_stream. */
+stev_status stev_mlp_eval(stev_mechanism *mech, const double *T, long n, float *props,
+                          void *cuda_stream);
+
 /* Number of resident solver slots (cells in flight) of the persistent kernel
  * on the current device for this mechanism and its options. */
 long stev_resident_slots(const stev_mechanism *mech);

@@ -27,6 +27,8 @@ EXPORTS = (
     "stev_default_options", "stev_mechanism_create", "stev_mechanism_set_options",
     "stev_mechanism_get_options", "stev_solve", "stev_solve_soa", "stev_solve_host",
     "stev_resident_slots", "stev_destroy", "stev_last_error", "stev_solve_host_noalloc",
+    "stev_mlp_num_params", "stev_mlp_train", "stev_mlp_set_params", "stev_mlp_get_params",
+    "stev_mlp_loss_grad", "stev_mlp_eval",
 )
 
 
@@ -74,6 +76,18 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [P, LNG, P, P, P, D, P, P, P, P, P]
             f.restype = I
+        L.stev_mlp_num_params.argtypes = [P]
+        L.stev_mlp_num_params.restype = LNG
+        L.stev_mlp_train.argtypes = [P, P, LNG, I, I, ctypes.c_float, ctypes.c_ulonglong, P]
+        L.stev_mlp_train.restype = I
+        L.stev_mlp_set_params.argtypes = [P, P, LNG, P, P]
+        L.stev_mlp_set_params.restype = I
+        L.stev_mlp_get_params.argtypes = [P, P, LNG, P, P]
+        L.stev_mlp_get_params.restype = I
+        L.stev_mlp_loss_grad.argtypes = [P, P, P, P, LNG, P, P]
+        L.stev_mlp_loss_grad.restype = I
+        L.stev_mlp_eval.argtypes = [P, P, LNG, P, P]
+        L.stev_mlp_eval.restype = I
         L.stev_resident_slots.argtypes = [P]
         L.stev_resident_slots.restype = LNG
         L.stev_destroy.argtypes = [P]
@@ -196,6 +210,51 @@ class Mechanism:
                                      float(dt), To.ctypes.data, Yo.ctypes.data, it.ctypes.data,
                                      st.ctypes.data, h))
         return To, Yo, it, st
+
+    # -- thermo network (Sec. 3) --------------------------------------------
+    @property
+    def mlp_num_params(self) -> int:
+        return int(lib().stev_mlp_num_params(self._h))
+
+    def mlp_train(self, T_samples, epochs: int = 30, batch: int = 4096, lr: float = 1e-3,
+                  seed: int = 0):
+        """Trains the thermo network on the GPU; returns the loss of every epoch."""
+        T = _np(T_samples, np.float64)
+        hist = np.zeros(epochs, np.float32)
+        _check(lib().stev_mlp_train(self._h, T.ctypes.data, len(T), int(epochs), int(batch),
+                                    float(lr), int(seed), hist.ctypes.data))
+        return hist
+
+    def mlp_params(self):
+        """(flat float32 parameters, mean [3S], std [3S])."""
+        n = self.mlp_num_params
+        p, mu, sd = np.zeros(n, np.float32), np.zeros(3 * self.S, np.float32), \
+            np.zeros(3 * self.S, np.float32)
+        _check(lib().stev_mlp_get_params(self._h, p.ctypes.data, n, mu.ctypes.data,
+                                         sd.ctypes.data))
+        return p, mu, sd
+
+    def mlp_set_params(self, params, mean, std):
+        p, mu, sd = _np(params, np.float32), _np(mean, np.float32), _np(std, np.float32)
+        _check(lib().stev_mlp_set_params(self._h, p.ctypes.data, len(p), mu.ctypes.data,
+                                         sd.ctypes.data))
+
+    def mlp_loss_grad(self, params, T, target):
+        """(loss, gradient) of the network on standardised targets, host arrays."""
+        p, Tn, tg = _np(params, np.float32), _np(T, np.float64), _np(target, np.float32)
+        g = np.zeros(len(p), np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(lib().stev_mlp_loss_grad(self._h, p.ctypes.data, Tn.ctypes.data, tg.ctypes.data,
+                                        len(Tn), g.ctypes.data, ctypes.addressof(loss)))
+        return loss.value, g
+
+    def mlp_eval(self, T, stream=None):
+        """Network values [n][3S] (cp/R, H/RT, S/R) at CUDA float64 temperatures."""
+        import torch
+        out = torch.empty((T.shape[0], 3 * self.S), dtype=torch.float32, device=T.device)
+        _check(lib().stev_mlp_eval(self._h, T.data_ptr(), T.shape[0], out.data_ptr(),
+                                   _stream_handle(stream)))
+        return out
 
     def close(self):
         if self._h:

@@ -16,6 +16,7 @@
 #include "stev_device.cuh"
 #include "stev_fp64.cuh"
 #include "stev_mixed.cuh"
+#include "stev_mlp.cuh"
 
 using namespace stev;
 
@@ -66,6 +67,13 @@ struct stev_mechanism {
   int* d_hit = nullptr;
   unsigned char* d_hst = nullptr;
   long long host_cap = 0;
+  // thermo network (Sec. 3)
+  int mlp_out = 0, mlp_out_pad = 0, mlp_np = 0;
+  float* d_mlp_params = nullptr;          // FP32 master parameters
+  __nv_bfloat16* d_mlp_W2 = nullptr;      // [64][64]
+  __nv_bfloat16* d_mlp_W3 = nullptr;      // [out_pad][64]
+  float* d_mlp_misc = nullptr;            // W1, b1, b2 [64 each], b3, mean, std [out_pad each]
+  bool mlp_ready = false;
 };
 
 extern "C" void stev_default_options(stev_options* o) {
@@ -110,7 +118,7 @@ static stev_status check_options(const stev_options* o) {
 
 static void free_mech(stev_mechanism* m) {
   void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
-                  m->d_twf, m->d_counter,
+                  m->d_twf, m->d_counter, m->d_mlp_params, m->d_mlp_W2, m->d_mlp_W3, m->d_mlp_misc,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -598,5 +606,276 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
   CUDA_TRY(cudaMemcpyAsync(iters, dit, nn * 4, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(cell_status, dst, nn, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  return STEV_OK;
+}
+
+// ------------------------------------------------------- thermo network
+static stev_status mlp_ensure(stev_mechanism* m) {
+  if (m->d_mlp_params) return STEV_OK;
+  m->mlp_out = 3 * m->S;
+  m->mlp_out_pad = (m->mlp_out + 7) / 8 * 8;
+  m->mlp_np = mlp_n_params(m->mlp_out);
+  CUDA_TRY(cudaMalloc(&m->d_mlp_params, (size_t)m->mlp_np * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&m->d_mlp_W2, (size_t)kHid * kHid * sizeof(__nv_bfloat16)));
+  CUDA_TRY(cudaMalloc(&m->d_mlp_W3, (size_t)m->mlp_out_pad * kHid * sizeof(__nv_bfloat16)));
+  CUDA_TRY(cudaMalloc(&m->d_mlp_misc, (size_t)(3 * kHid + 3 * m->mlp_out_pad) * sizeof(float)));
+  return STEV_OK;
+}
+
+// FP32 master parameters (host copy) + standardisation -> inference buffers
+static stev_status mlp_pack(stev_mechanism* m, const std::vector<float>& P,
+                            const std::vector<float>& mean, const std::vector<float>& stdv) {
+  const MlpOffsets o = mlp_offsets(m->mlp_out);
+  std::vector<__nv_bfloat16> w2((size_t)kHid * kHid), w3((size_t)m->mlp_out_pad * kHid);
+  for (int k = 0; k < kHid * kHid; ++k) w2[k] = __float2bfloat16_rn(P[o.W2 + k]);
+  for (int r = 0; r < m->mlp_out_pad; ++r)
+    for (int k = 0; k < kHid; ++k)
+      w3[(size_t)r * kHid + k] = __float2bfloat16_rn(r < m->mlp_out ? P[o.W3 + r * kHid + k] : 0.0f);
+  std::vector<float> misc((size_t)3 * kHid + 3 * m->mlp_out_pad, 0.0f);
+  for (int k = 0; k < kHid; ++k) {
+    misc[k] = P[o.W1 + k];
+    misc[kHid + k] = P[o.b1 + k];
+    misc[2 * kHid + k] = P[o.b2 + k];
+  }
+  float* b3 = misc.data() + 3 * kHid;
+  float* mu = b3 + m->mlp_out_pad;
+  float* sd = mu + m->mlp_out_pad;
+  for (int r = 0; r < m->mlp_out_pad; ++r) {
+    b3[r] = r < m->mlp_out ? P[o.b3 + r] : 0.0f;
+    mu[r] = r < m->mlp_out ? mean[r] : 0.0f;
+    sd[r] = r < m->mlp_out ? stdv[r] : 1.0f;
+  }
+  CUDA_TRY(cudaMemcpy(m->d_mlp_params, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_mlp_W2, w2.data(), w2.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_mlp_W3, w3.data(), w3.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_mlp_misc, misc.data(), misc.size() * sizeof(float), cudaMemcpyHostToDevice));
+  m->mlp_ready = true;
+  return STEV_OK;
+}
+
+static MlpInfer mlp_infer_view(const stev_mechanism* m) {
+  MlpInfer w;
+  w.W2 = m->d_mlp_W2;
+  w.W3 = m->d_mlp_W3;
+  w.W1 = m->d_mlp_misc;
+  w.b1 = m->d_mlp_misc + kHid;
+  w.b2 = m->d_mlp_misc + 2 * kHid;
+  w.b3 = m->d_mlp_misc + 3 * kHid;
+  w.mean = w.b3 + m->mlp_out_pad;
+  w.stdv = w.mean + m->mlp_out_pad;
+  w.n_out = m->mlp_out_pad;
+  w.n_valid = m->mlp_out;
+  return w;
+}
+
+extern "C" long stev_mlp_num_params(const stev_mechanism* m) {
+  return m ? (long)mlp_n_params(3 * m->S) : 0;
+}
+
+extern "C" stev_status stev_mlp_set_params(stev_mechanism* m, const float* params, long n_params,
+                                           const float* mean, const float* stdv) {
+  g_err.clear();
+  if (!m || !params || !mean || !stdv) return fail(STEV_EINVAL, "NULL argument");
+  if (n_params != mlp_n_params(3 * m->S))
+    return fail(STEV_EINVAL, "expected %d parameters, got %ld", mlp_n_params(3 * m->S), n_params);
+  for (long k = 0; k < n_params; ++k)
+    if (!std::isfinite(params[k])) return fail(STEV_EINVAL, "parameter %ld not finite", k);
+  for (int r = 0; r < 3 * m->S; ++r)
+    if (!std::isfinite(mean[r]) || !(stdv[r] > 0.0f)) return fail(STEV_EINVAL, "bad standardisation %d", r);
+  stev_status st = mlp_ensure(m);
+  if (st != STEV_OK) return st;
+  std::vector<float> P(params, params + n_params), mu(mean, mean + 3 * m->S), sd(stdv, stdv + 3 * m->S);
+  return mlp_pack(m, P, mu, sd);
+}
+
+extern "C" stev_status stev_mlp_get_params(const stev_mechanism* m, float* params, long n_params,
+                                           float* mean, float* stdv) {
+  g_err.clear();
+  if (!m || !params || !mean || !stdv) return fail(STEV_EINVAL, "NULL argument");
+  if (!m->mlp_ready) return fail(STEV_EINVAL, "the thermo network has not been trained or set");
+  if (n_params != m->mlp_np) return fail(STEV_EINVAL, "expected %d parameters", m->mlp_np);
+  CUDA_TRY(cudaMemcpy(params, m->d_mlp_params, (size_t)n_params * sizeof(float), cudaMemcpyDeviceToHost));
+  const float* base = m->d_mlp_misc + 3 * kHid + m->mlp_out_pad;
+  CUDA_TRY(cudaMemcpy(mean, base, (size_t)m->mlp_out * sizeof(float), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(stdv, base + m->mlp_out_pad, (size_t)m->mlp_out * sizeof(float), cudaMemcpyDeviceToHost));
+  return STEV_OK;
+}
+
+// Gradient of the mean-squared error of the network with parameters
+// `params` on n samples (standardised targets), through the training kernel.
+static stev_status mlp_grad_device(stev_mechanism* m, const float* d_params, const double* d_T,
+                                   const float* d_target, long long n, long long n_total,
+                                   float* d_grad, double* d_loss, cudaStream_t s) {
+  const size_t smem = mlp_grad_smem_bytes(m->mlp_out);
+  CUDA_TRY(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int blocks = (int)((n + kMlpTile - 1) / kMlpTile);
+  mlp_grad_kernel<<<blocks, kMlpTile, smem, s>>>(d_params, m->mlp_out, d_T, d_target, n, n_total,
+                                                 d_grad, d_loss);
+  CUDA_TRY(cudaGetLastError());
+  return STEV_OK;
+}
+
+extern "C" stev_status stev_mlp_loss_grad(stev_mechanism* m, const float* params, const double* T,
+                                          const float* target, long n, float* grad,
+                                          double* loss) {
+  g_err.clear();
+  if (!m || !params || !T || !target || !grad || !loss) return fail(STEV_EINVAL, "NULL argument");
+  if (n < 1) return fail(STEV_EINVAL, "n < 1");
+  const int np = mlp_n_params(3 * m->S), no = 3 * m->S;
+  m->mlp_out = no;
+  float *dp = nullptr, *dt = nullptr, *dg = nullptr;
+  double *dT = nullptr, *dl = nullptr;
+  stev_status st = STEV_OK;
+  auto cleanup = [&]() { cudaFree(dp); cudaFree(dt); cudaFree(dg); cudaFree(dT); cudaFree(dl); };
+#define TRY_CLEAN(expr)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cleanup();                                                                            \
+      return fail(STEV_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));                     \
+    }                                                                                       \
+  } while (0)
+  TRY_CLEAN(cudaMalloc(&dp, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dg, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dt, (size_t)n * no * 4));
+  TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
+  TRY_CLEAN(cudaMalloc(&dl, 8));
+  TRY_CLEAN(cudaMemcpy(dp, params, (size_t)np * 4, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemcpy(dt, target, (size_t)n * no * 4, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemcpy(dT, T, (size_t)n * 8, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemset(dg, 0, (size_t)np * 4));
+  TRY_CLEAN(cudaMemset(dl, 0, 8));
+  st = mlp_grad_device(m, dp, dT, dt, n, n, dg, dl, 0);
+  if (st == STEV_OK) {
+    TRY_CLEAN(cudaMemcpy(grad, dg, (size_t)np * 4, cudaMemcpyDeviceToHost));
+    TRY_CLEAN(cudaMemcpy(loss, dl, 8, cudaMemcpyDeviceToHost));
+    *loss /= (double)n * no;
+  }
+#undef TRY_CLEAN
+  cleanup();
+  return st;
+}
+
+static inline uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples, long n,
+                                      int epochs, int batch, float lr, unsigned long long seed,
+                                      float* loss_per_epoch) {
+  g_err.clear();
+  if (!m || !T_samples) return fail(STEV_EINVAL, "NULL argument");
+  if (n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f)) return fail(STEV_EINVAL, "bad training sizes");
+  for (long k = 0; k < n; ++k)
+    if (!(T_samples[k] > 0.0) || !std::isfinite(T_samples[k])) return fail(STEV_EINVAL, "T_samples[%ld] invalid", k);
+  stev_status st = mlp_ensure(m);
+  if (st != STEV_OK) return st;
+  const int no = m->mlp_out, np = m->mlp_np;
+  double *dT = nullptr, *dsum = nullptr, *dloss = nullptr;
+  float *dtarget = nullptr, *dgrad = nullptr, *dm1 = nullptr, *dm2 = nullptr, *dstat = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dT); cudaFree(dsum); cudaFree(dloss); cudaFree(dtarget); cudaFree(dgrad);
+    cudaFree(dm1); cudaFree(dm2); cudaFree(dstat);
+  };
+#define TRY_CLEAN(expr)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cleanup();                                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? STEV_ENOMEM : STEV_ECUDA, "%s: %s",     \
+                  #expr, cudaGetErrorString(e_));                                           \
+    }                                                                                       \
+  } while (0)
+  TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
+  TRY_CLEAN(cudaMalloc(&dtarget, (size_t)n * no * 4));
+  TRY_CLEAN(cudaMalloc(&dsum, (size_t)2 * no * 8));
+  TRY_CLEAN(cudaMalloc(&dstat, (size_t)2 * no * 4));
+  TRY_CLEAN(cudaMalloc(&dgrad, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dm1, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dm2, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dloss, 8));
+  TRY_CLEAN(cudaMemcpy(dT, T_samples, (size_t)n * 8, cudaMemcpyHostToDevice));
+  // targets: the polynomials in FP64, standardised per output column
+  {
+    const long long tot = (long long)n * m->S;
+    mlp_targets_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(m->d_sp, m->S, dT, n, dtarget);
+    TRY_CLEAN(cudaGetLastError());
+    TRY_CLEAN(cudaMemset(dsum, 0, (size_t)2 * no * 8));
+    mlp_moments_kernel<<<dim3(64, no), 256>>>(dtarget, n, no, dsum, dsum + no);
+    TRY_CLEAN(cudaGetLastError());
+  }
+  std::vector<double> sums((size_t)2 * no);
+  TRY_CLEAN(cudaMemcpy(sums.data(), dsum, sums.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<float> mean(no), stdv(no), inv(no);
+  for (int c = 0; c < no; ++c) {
+    const double mu = sums[c] / n;
+    const double var = std::max(sums[no + c] / n - mu * mu, 0.0);
+    mean[c] = (float)mu;
+    stdv[c] = (float)std::max(std::sqrt(var), 1e-6 * std::max(1.0, std::fabs(mu)));
+    inv[c] = 1.0f / stdv[c];
+  }
+  TRY_CLEAN(cudaMemcpy(dstat, mean.data(), no * 4, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemcpy(dstat + no, inv.data(), no * 4, cudaMemcpyHostToDevice));
+  {
+    const long long tot = (long long)n * no;
+    mlp_standardise_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(dtarget, n, no, dstat, dstat + no);
+    TRY_CLEAN(cudaGetLastError());
+  }
+  // Xavier-uniform initialisation from splitmix64(seed), zero biases
+  const MlpOffsets o = mlp_offsets(no);
+  std::vector<float> P(np, 0.0f);
+  uint64_t rs = seed;
+  auto uni = [&](float a) { return (float)(((splitmix64(rs) >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0) * a; };
+  for (int k = 0; k < kHid; ++k) P[o.W1 + k] = uni(std::sqrt(6.0f / (1 + kHid)));
+  for (int k = 0; k < kHid * kHid; ++k) P[o.W2 + k] = uni(std::sqrt(6.0f / (kHid + kHid)));
+  for (int k = 0; k < no * kHid; ++k) P[o.W3 + k] = uni(std::sqrt(6.0f / (kHid + no)));
+  TRY_CLEAN(cudaMemcpy(m->d_mlp_params, P.data(), (size_t)np * 4, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemset(dgrad, 0, (size_t)np * 4));
+  TRY_CLEAN(cudaMemset(dm1, 0, (size_t)np * 4));
+  TRY_CLEAN(cudaMemset(dm2, 0, (size_t)np * 4));
+  // Adam over minibatches in sample order (the samples are drawn independently)
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  long long step = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    TRY_CLEAN(cudaMemset(dloss, 0, 8));
+    for (long long s0 = 0; s0 < n; s0 += batch) {
+      const long long nb = std::min((long long)batch, (long long)n - s0);
+      st = mlp_grad_device(m, m->d_mlp_params, dT + s0, dtarget + s0 * no, nb, nb, dgrad, dloss, 0);
+      if (st != STEV_OK) { cleanup(); return st; }
+      ++step;
+      // the loss accumulated by each minibatch is its own mean; average below
+      const float bc1 = 1.0f - std::pow(b1, (float)step), bc2 = 1.0f - std::pow(b2, (float)step);
+      mlp_adam_kernel<<<(np + 255) / 256, 256>>>(m->d_mlp_params, dgrad, dm1, dm2, np, lr, b1, b2, eps, bc1, bc2);
+      TRY_CLEAN(cudaGetLastError());
+    }
+    if (loss_per_epoch) {
+      double l = 0.0;
+      TRY_CLEAN(cudaMemcpy(&l, dloss, 8, cudaMemcpyDeviceToHost));
+      loss_per_epoch[ep] = (float)(l / ((double)n * no));
+    }
+  }
+  TRY_CLEAN(cudaMemcpy(P.data(), m->d_mlp_params, (size_t)np * 4, cudaMemcpyDeviceToHost));
+#undef TRY_CLEAN
+  cleanup();
+  return mlp_pack(m, P, mean, stdv);
+}
+
+extern "C" stev_status stev_mlp_eval(stev_mechanism* m, const double* T, long n, float* props,
+                                     void* stream) {
+  g_err.clear();
+  if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (!m->mlp_ready) return fail(STEV_EINVAL, "the thermo network has not been trained or set");
+  if (n < 0) return fail(STEV_EINVAL, "n < 0");
+  if (n == 0) return STEV_OK;
+  if (!T || !props) return fail(STEV_EINVAL, "NULL array");
+  const int warps = 8;
+  const size_t smem = mlp_eval_smem_bytes(warps);
+  const long long groups = (n + 15) / 16;
+  const int blocks = (int)std::min<long long>((groups + warps - 1) / warps, 148LL * 16);
+  mlp_eval_kernel<<<blocks, warps * 32, smem, (cudaStream_t)stream>>>(mlp_infer_view(m), T, n, props);
+  CUDA_TRY(cudaGetLastError());
   return STEV_OK;
 }

@@ -1,0 +1,352 @@
+// Thermo network (Sec. 3: a neural network of temperature stands in for the
+// NASA-7 species properties): training and inference kernels.
+//
+// Network: t = (T - 1650)/1350, a1 = tanh(W1 t + b1) [64],
+// a2 = tanh(W2 a1 + b2) [64], y = W3 a2 + b3 [3S] standardised outputs
+// (cp/R of every species, then H/RT, then S/R), value = y * std + mean.
+// Parameters are one flat FP32 array in the order W1[64], b1[64], W2[64][64],
+// b2[64], W3[3S][64], b3[3S] (rows = outputs).
+//
+// Training (FP32, off the hot path): one fused kernel per minibatch computes
+// the forward pass, the mean-squared-error gradient and the weight gradients
+// of a 64-sample tile entirely in shared memory and adds them to a global
+// gradient buffer; an Adam kernel then updates the parameters.
+// Inference (BF16 weights and activations, FP32 accumulation): warp-level
+// tensor-core MMAs m16n8k16 on 16 temperatures at a time.
+#pragma once
+#include <cuda_bf16.h>
+#include "stev_device.cuh"
+
+namespace stev {
+
+constexpr int kHid = 64;
+constexpr float kTMid = 1650.0f, kTHalf = 1350.0f;
+constexpr int kMlpTile = 64;  // samples per CTA in training
+
+__host__ __device__ inline int mlp_n_params(int n_out) {
+  return kHid + kHid + kHid * kHid + kHid + n_out * kHid + n_out;
+}
+struct MlpOffsets {
+  int W1, b1, W2, b2, W3, b3, total;
+};
+__host__ __device__ inline MlpOffsets mlp_offsets(int n_out) {
+  MlpOffsets o;
+  o.W1 = 0;
+  o.b1 = o.W1 + kHid;
+  o.W2 = o.b1 + kHid;
+  o.b2 = o.W2 + kHid * kHid;
+  o.W3 = o.b2 + kHid;
+  o.b3 = o.W3 + n_out * kHid;
+  o.total = o.b3 + n_out;
+  return o;
+}
+
+// ----------------------------------------------------- training targets
+// NASA-7 properties (Eqs. 15-16, S/R = H/RT - G/RT) of every species at every
+// sample temperature, in FP64, stored as float: out[s][o], o = i, S+i, 2S+i.
+__global__ void mlp_targets_kernel(const double* __restrict__ sp_tab, int S,
+                                   const double* __restrict__ T, long long n,
+                                   float* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * S) return;
+  const long long s = idx / S;
+  const int i = (int)(idx - s * S);
+  const double t = T[s];
+  const double* sp = sp_tab + i * SP_STRIDE;
+  const double* b = sp + (t < sp[SP_TSPLIT] ? SP_LOW : SP_HIGH);
+  const double lnT = log(t), invT = 1.0 / t;
+  const double cpR = fma(fma(fma(fma(b[B_A4], t, b[B_A3]), t, b[B_A2]), t, b[B_A1]), t, b[B_A0]);
+  const double hp = fma(fma(fma(b[B_H4], t, b[B_H3]), t, b[B_H2]), t, b[B_H1]);
+  const double hRT = fma(hp, t, b[B_A0]) + b[B_A5] * invT;
+  const double gp = fma(fma(fma(b[B_G4], t, b[B_G3]), t, b[B_G2]), t, b[B_H1]);
+  const double gRT = fma(b[B_A0], 1.0 - lnT, fma(b[B_A5], invT, -b[B_A6])) - gp * t;
+  float* o = out + s * (3 * S);
+  o[i] = (float)cpR;
+  o[S + i] = (float)hRT;
+  o[2 * S + i] = (float)(hRT - gRT);
+}
+
+// column sums and sums of squares (FP64 accumulation) for standardisation
+__global__ void mlp_moments_kernel(const float* __restrict__ v, long long n, int m,
+                                   double* __restrict__ sum, double* __restrict__ sum2) {
+  const int col = blockIdx.y;
+  double a = 0.0, b = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const double x = v[r * m + col];
+    a += x;
+    b += x * x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sum + col, a);
+    atomicAdd(sum2 + col, b);
+  }
+}
+
+__global__ void mlp_standardise_kernel(float* __restrict__ v, long long n, int m,
+                                       const float* __restrict__ mean,
+                                       const float* __restrict__ inv_std) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * m) return;
+  const int col = (int)(idx % m);
+  v[idx] = (v[idx] - mean[col]) * inv_std[col];
+}
+
+// ------------------------------------------------ fused forward + backward
+// One CTA of kMlpTile threads: thread s owns sample s of the tile.  Shared
+// memory: the parameters, then feature-major activations a1, a2, dz1, dz2
+// [64][tile+1] and dy [n_out][tile+1] (the +1 keeps rows on distinct banks).
+// Adds d loss / d params to grad and the tile's sum of squared errors to
+// loss_sum; the loss is the mean over n_total samples and n_out outputs.
+__global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
+    const float* __restrict__ params, int n_out, const double* __restrict__ T,
+    const float* __restrict__ target, long long n, long long n_total, float* __restrict__ grad,
+    double* __restrict__ loss_sum) {
+  extern __shared__ __align__(16) float sm[];
+  const MlpOffsets off = mlp_offsets(n_out);
+  float* P = sm;
+  const int ld = kMlpTile + 1;
+  float* a1 = P + off.total;
+  float* a2 = a1 + kHid * ld;
+  float* z1 = a2 + kHid * ld;   // dz1
+  float* z2 = z1 + kHid * ld;   // dz2
+  float* dy = z2 + kHid * ld;   // [n_out][ld]
+  float* ts = dy + n_out * ld;  // [tile]
+  for (int k = threadIdx.x; k < off.total; k += blockDim.x) P[k] = params[k];
+  const long long s0 = (long long)blockIdx.x * kMlpTile;
+  const int s = threadIdx.x;
+  const bool valid = s0 + s < n;
+  __syncthreads();
+
+  // forward
+  const float t = valid ? ((float)T[s0 + s] - kTMid) / kTHalf : 0.0f;
+  ts[s] = t;
+  for (int j = 0; j < kHid; ++j) a1[j * ld + s] = tanhf(fmaf(P[off.W1 + j], t, P[off.b1 + j]));
+  for (int j = 0; j < kHid; ++j) {
+    float acc = P[off.b2 + j];
+    for (int k = 0; k < kHid; ++k) acc = fmaf(P[off.W2 + j * kHid + k], a1[k * ld + s], acc);
+    a2[j * ld + s] = tanhf(acc);
+  }
+  const float scale = 2.0f / (float)((double)n_total * n_out);
+  double se = 0.0;
+  for (int o = 0; o < n_out; ++o) {
+    float acc = P[off.b3 + o];
+    for (int k = 0; k < kHid; ++k) acc = fmaf(P[off.W3 + o * kHid + k], a2[k * ld + s], acc);
+    const float d = valid ? acc - target[(s0 + s) * n_out + o] : 0.0f;
+    se += (double)d * d;
+    dy[o * ld + s] = d * scale;
+  }
+  // backward through the activations
+  for (int j = 0; j < kHid; ++j) {
+    float acc = 0.0f;
+    for (int o = 0; o < n_out; ++o) acc = fmaf(P[off.W3 + o * kHid + j], dy[o * ld + s], acc);
+    const float a = a2[j * ld + s];
+    z2[j * ld + s] = acc * (1.0f - a * a);
+  }
+  for (int j = 0; j < kHid; ++j) {
+    float acc = 0.0f;
+    for (int o = 0; o < kHid; ++o) acc = fmaf(P[off.W2 + o * kHid + j], z2[o * ld + s], acc);
+    const float a = a1[j * ld + s];
+    z1[j * ld + s] = acc * (1.0f - a * a);
+  }
+  for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, se);
+  __syncthreads();
+
+  // weight gradients: sums over the tile's samples
+  const int nt = (int)min((long long)kMlpTile, n - s0);
+  for (int k = threadIdx.x; k < off.total; k += blockDim.x) {
+    float acc = 0.0f;
+    if (k < off.b1) {                       // W1[j], input t
+      const int j = k - off.W1;
+      for (int q = 0; q < nt; ++q) acc = fmaf(z1[j * ld + q], ts[q], acc);
+    } else if (k < off.W2) {                // b1
+      const int j = k - off.b1;
+      for (int q = 0; q < nt; ++q) acc += z1[j * ld + q];
+    } else if (k < off.b2) {                // W2[j][i]
+      const int j = (k - off.W2) / kHid, i = (k - off.W2) % kHid;
+      for (int q = 0; q < nt; ++q) acc = fmaf(z2[j * ld + q], a1[i * ld + q], acc);
+    } else if (k < off.W3) {                // b2
+      const int j = k - off.b2;
+      for (int q = 0; q < nt; ++q) acc += z2[j * ld + q];
+    } else if (k < off.b3) {                // W3[o][i]
+      const int o = (k - off.W3) / kHid, i = (k - off.W3) % kHid;
+      for (int q = 0; q < nt; ++q) acc = fmaf(dy[o * ld + q], a2[i * ld + q], acc);
+    } else {                                // b3
+      const int o = k - off.b3;
+      for (int q = 0; q < nt; ++q) acc += dy[o * ld + q];
+    }
+    atomicAdd(grad + k, acc);
+  }
+}
+
+__host__ __device__ inline size_t mlp_grad_smem_bytes(int n_out) {
+  return ((size_t)mlp_n_params(n_out) + (size_t)(4 * kHid + n_out) * (kMlpTile + 1) + kMlpTile) *
+         sizeof(float);
+}
+
+// Adam (Kingma & Ba 2015) on every parameter; clears the gradient.
+__global__ void mlp_adam_kernel(float* __restrict__ p, float* __restrict__ g,
+                                float* __restrict__ m1, float* __restrict__ m2, int n, float lr,
+                                float beta1, float beta2, float eps, float bc1, float bc2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float gk = g[k];
+  const float a = beta1 * m1[k] + (1.0f - beta1) * gk;
+  const float b = beta2 * m2[k] + (1.0f - beta2) * gk * gk;
+  m1[k] = a;
+  m2[k] = b;
+  p[k] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+  g[k] = 0.0f;
+}
+
+// ------------------------------------------------------------- inference
+// Inference weights: W2 and W3 rows in BF16 (row-major [out][in]: a row of W
+// is a column of the MMA's B operand, so B fragments are direct 32-bit loads),
+// W1, b1, b2, b3, mean, std in FP32.
+struct MlpInfer {
+  const __nv_bfloat16* W2;  // [64][64]
+  const __nv_bfloat16* W3;  // [n_out][64]
+  const float* W1;          // [64]
+  const float* b1;          // [64]
+  const float* b2;          // [64]
+  const float* b3;          // [n_out]
+  const float* mean;        // [n_out]
+  const float* stdv;        // [n_out]
+  int n_out;                // padded to a multiple of 8
+  int n_valid;              // 3S: columns written to the caller's array
+};
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float* d, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// One warp evaluates the network at 16 temperatures (rows).  act is a warp-
+// private shared buffer of 16 x (64+8) BF16 for the activations.  out[r][o]
+// receives value(o) for o in [o_begin, o_end) (a multiple of 8 wide), rows
+// r < n_rows; out_ld is the row stride of out.
+__device__ void mlp_eval_warp16(const MlpInfer& w, const float* t16, __nv_bfloat16* act,
+                                float* out, int out_ld, int n_rows, int o_begin, int o_end) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  constexpr int lda = kHid + 8;  // BF16 elements per activation row
+  // layer 1 (1 -> 64) on the SIMT pipes: lane handles 2 hidden units for all rows
+  for (int r = 0; r < 16; ++r) {
+    const int j = lane * 2;
+    const float t = t16[r];
+    const float h0 = tanh_approx(fmaf(w.W1[j], t, w.b1[j]));
+    const float h1 = tanh_approx(fmaf(w.W1[j + 1], t, w.b1[j + 1]));
+    *reinterpret_cast<unsigned*>(act + r * lda + j) = pack_bf16(h0, h1);
+  }
+  __syncwarp();
+  // layer 2 (64 -> 64): 8 n-tiles x 4 k-steps of m16n8k16
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float b0 = w.b2[nt * 8 + tg * 2], b1v = w.b2[nt * 8 + tg * 2 + 1];
+    acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
+  }
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const int k0 = ks * 16;
+    unsigned a[4];
+    a[0] = *reinterpret_cast<const unsigned*>(act + g * lda + k0 + tg * 2);
+    a[1] = *reinterpret_cast<const unsigned*>(act + (g + 8) * lda + k0 + tg * 2);
+    a[2] = *reinterpret_cast<const unsigned*>(act + g * lda + k0 + 8 + tg * 2);
+    a[3] = *reinterpret_cast<const unsigned*>(act + (g + 8) * lda + k0 + 8 + tg * 2);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const __nv_bfloat16* wr = w.W2 + (nt * 8 + g) * kHid + k0 + tg * 2;
+      unsigned b[2];
+      b[0] = __ldg(reinterpret_cast<const unsigned*>(wr));
+      b[1] = __ldg(reinterpret_cast<const unsigned*>(wr + 8));
+      mma_bf16_16816(acc[nt], a, b);
+    }
+  }
+  __syncwarp();
+  // tanh, back to BF16 in the same buffer (every lane has finished reading it)
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int c = nt * 8 + tg * 2;
+    *reinterpret_cast<unsigned*>(act + g * lda + c) =
+        pack_bf16(tanh_approx(acc[nt][0]), tanh_approx(acc[nt][1]));
+    *reinterpret_cast<unsigned*>(act + (g + 8) * lda + c) =
+        pack_bf16(tanh_approx(acc[nt][2]), tanh_approx(acc[nt][3]));
+  }
+  __syncwarp();
+  // layer 3 (64 -> outputs), one n-tile of 8 outputs at a time
+  unsigned a[4][4];
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const int k0 = ks * 16;
+    a[ks][0] = *reinterpret_cast<const unsigned*>(act + g * lda + k0 + tg * 2);
+    a[ks][1] = *reinterpret_cast<const unsigned*>(act + (g + 8) * lda + k0 + tg * 2);
+    a[ks][2] = *reinterpret_cast<const unsigned*>(act + g * lda + k0 + 8 + tg * 2);
+    a[ks][3] = *reinterpret_cast<const unsigned*>(act + (g + 8) * lda + k0 + 8 + tg * 2);
+  }
+  for (int o0 = o_begin; o0 < o_end; o0 += 8) {
+    const int c = o0 + tg * 2;
+    float d[4] = {w.b3[c], w.b3[c + 1], w.b3[c], w.b3[c + 1]};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const __nv_bfloat16* wr = w.W3 + (o0 + g) * kHid + ks * 16 + tg * 2;
+      unsigned b[2];
+      b[0] = __ldg(reinterpret_cast<const unsigned*>(wr));
+      b[1] = __ldg(reinterpret_cast<const unsigned*>(wr + 8));
+      mma_bf16_16816(d, a[ks], b);
+    }
+    const float m0 = w.mean[c], m1 = w.mean[c + 1], s0 = w.stdv[c], s1 = w.stdv[c + 1];
+    const bool c0ok = c < w.n_valid, c1ok = c + 1 < w.n_valid;
+    if (g < n_rows) {
+      if (c0ok) out[g * out_ld + c - o_begin] = fmaf(d[0], s0, m0);
+      if (c1ok) out[g * out_ld + c + 1 - o_begin] = fmaf(d[1], s1, m1);
+    }
+    if (g + 8 < n_rows) {
+      if (c0ok) out[(g + 8) * out_ld + c - o_begin] = fmaf(d[2], s0, m0);
+      if (c1ok) out[(g + 8) * out_ld + c + 1 - o_begin] = fmaf(d[3], s1, m1);
+    }
+  }
+  __syncwarp();
+}
+
+// Batched inference: every warp takes 16 temperatures.  out [n][n_out].
+__global__ void mlp_eval_kernel(MlpInfer w, const double* __restrict__ T, long long n,
+                                float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(smem) + warp * 16 * (kHid + 8);
+  float* t16 = reinterpret_cast<float*>(smem + (blockDim.x / 32) * 16 * (kHid + 8) * 2) + warp * 16;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 16; base < n;
+       base += nwarps * 16) {
+    if (lane < 16) t16[lane] = base + lane < n ? ((float)T[base + lane] - kTMid) / kTHalf : 0.0f;
+    __syncwarp();
+    const int rows = (int)min((long long)16, n - base);
+    mlp_eval_warp16(w, t16, act, out + base * w.n_valid, w.n_valid, rows, 0, w.n_out);
+  }
+}
+
+__host__ inline size_t mlp_eval_smem_bytes(int warps) {
+  return (size_t)warps * 16 * (kHid + 8) * 2 + (size_t)warps * 16 * 4;
+}
+
+}  // namespace stev
