@@ -238,6 +238,18 @@ def run_ours(args):
     extra = {} if args.max_iters is None else {"max_iters": args.max_iters}
     prec = binding.MIXED if args.precision == "mixed" else binding.FP64
     m = Mechanism(mech, precision=prec, **extra)
+    mlp_info = None
+    if args.thermo == "mlp":
+        if args.precision != "mixed":
+            raise SystemExit("--thermo mlp needs --precision mixed")
+        t0 = time.time()
+        Ts = np.random.default_rng(2024).uniform(300.0, 3000.0, size=args.mlp_samples)
+        hist = m.mlp_train(Ts, epochs=args.mlp_epochs, batch=4096, lr=2e-3, seed=7)
+        m.set_options(thermo=binding.THERMO_MLP)
+        mlp_info = {"net": "1-64-64-%d tanh, BF16 weights, FP32 accumulate" % (3 * S),
+                    "train_samples": args.mlp_samples, "epochs": args.mlp_epochs,
+                    "final_loss": float(hist[-1]), "train_s": time.time() - t0,
+                    "supplies": "cp/R and H/RT (energy equation), 300-3000 K"}
     n = len(T)
     Td, Pd, Yd = (torch.from_numpy(a).to(dev) for a in (T, P, Y))
     out = (torch.empty_like(Td), torch.empty_like(Yd), torch.empty(n, dtype=torch.int32, device=dev),
@@ -338,7 +350,8 @@ def run_ours(args):
             "config": {"workload": "syn32x150 (32 species, 150 reversible reactions), %d cells "
                                    "per GPU, T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), "
                                    "dt 1e-3 s" % n,
-                       "precision": args.precision, "thermo": "NASA-7 polynomial",
+                       "precision": args.precision,
+                       "thermo": "network" if args.thermo == "mlp" else "NASA-7 polynomial",
                        "cells_per_gpu": n, "warmup_cells": nw, "max_iters": extra.get(
                            "max_iters", 200000),
                        "l2": "inputs (%d MB) larger than L2" % ((T.nbytes + P.nbytes + Y.nbytes)
@@ -350,7 +363,7 @@ def run_ours(args):
             "cell_status": {"ok": int(status[0]), "maxiter": int(status[1]),
                             "nonfinite": int(status[2]), "trange": int(status[3])},
             "roofline": roofline, "gpu_launches": args.steps, "e2e": e2e,
-            "plain_fp64": plain, "wall_s_timed": wall}
+            "plain_fp64": plain, "thermo_net": mlp_info, "wall_s_timed": wall}
     line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **extra)
@@ -365,6 +378,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--thermo", choices=["poly", "mlp"], default="poly")
+    ap.add_argument("--mlp-samples", type=int, default=1_000_000)
+    ap.add_argument("--mlp-epochs", type=int, default=30)
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 solve of the same cells (mixed runs only)")
     ap.add_argument("--cells", type=int, default=N_CELLS)

@@ -50,7 +50,11 @@ enum {
 };
 
 enum { STEV_FP64 = 0, STEV_MIXED = 1 };            /* options.precision */
-enum { STEV_THERMO_POLY = 0, STEV_THERMO_MLP = 1 }; /* options.thermo */
+/* options.thermo: where the mixed path takes species properties from.
+ * POLY: NASA-7 polynomials.  MLP: cp/R from the thermo network, H/RT and G/RT
+ * from the polynomials.  MLP_CPH: cp/R and H/RT from the network.  G/RT (the
+ * equilibrium constants of Eq. 30) always comes from the FP64 polynomials. */
+enum { STEV_THERMO_POLY = 0, STEV_THERMO_MLP = 1, STEV_THERMO_MLP_CPH = 2 };
 
 /* Solver parameters.  The paper names them but gives values for few; the
  * defaults (stev_default_options) are the readings listed beside each. */
@@ -66,7 +70,7 @@ typedef struct {
   double rof_min;     /* lower clamp keeping rOF > 0 (1e-30) */
   int max_iters;      /* per-cell iteration cap (200000) */
   int precision;      /* STEV_FP64 or STEV_MIXED */
-  int thermo;         /* STEV_THERMO_POLY or STEV_THERMO_MLP */
+  int thermo;         /* STEV_THERMO_POLY, _MLP or _MLP_CPH (POLY) */
   int dft_on;         /* 0 disables the Sec. 2.3 damper (1) */
   int lanes_per_cell; /* lanes that share one cell: 8, 16 or 32; 0 = chosen per
                          mechanism and precision (0) */
@@ -161,8 +165,9 @@ stev_status stev_solve_host_noalloc(stev_mechanism *mech, long n_cells, const do
 /* ---- thermo network (Sec. 3: a small neural network of temperature stands in
  * for the NASA-7 species properties; Figs. 2-3).  The library's network is
  * t = (T - 1650)/1350, a1 = tanh(W1 t + b1), a2 = tanh(W2 a1 + b2) (64 each),
- * y = W3 a2 + b3 (3S standardised outputs: cp/R of every species, then H/RT,
- * then S/R; value = y * std + mean).  Parameters are one flat float array:
+ * y = W3 a2 + b3 (3S standardised outputs: cp/R of every species, then H/R
+ * in kelvin (H/RT times T, smooth over the range), then S/R; value =
+ * y * std + mean).  Parameters are one flat float array:
  * W1[64], b1[64], W2[64][64], b2[64], W3[3S][64], b3[3S] (rows = outputs). */
 
 /* Number of network parameters of this mechanism (64*64 + 67*3S + 192). */
@@ -194,7 +199,7 @@ stev_status stev_mlp_loss_grad(stev_mechanism *mech, const float *params, const 
 
 /* Evaluates the trained network (BF16 tensor-core MMAs, FP32 accumulation) at
  * n DEVICE temperatures; props (DEVICE) receives [n][3S] values (cp/R, H/RT,
- * S/R).  Asynchronous on cuda_stream. */
+ * S/R) in the order above.  Asynchronous on cuda_stream. */
 stev_status stev_mlp_eval(stev_mechanism *mech, const double *T, long n, float *props,
                           void *cuda_stream);
 

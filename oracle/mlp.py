@@ -11,8 +11,9 @@ can check the GPU's forward pass, loss and gradients against it:
     y  = W3 a2 + b3                               3S standardised outputs
     loss = mean over samples and outputs of (y - target)^2
 
-Targets are the polynomial values (cp/R, H/RT, S/R of every species, in that
-order) standardised per output column: (value - mean) / std.  Parameters are
+Targets are the polynomial values (cp/R, H/R = H/RT * T in kelvin, S/R of
+every species, in that order) standardised per output column:
+(value - mean) / std.  Parameters are
 a dict of arrays W1 [64][1], b1 [64], W2 [64][64], b2 [64], W3 [3S][64],
 b3 [3S] (rows = outputs), flattened in that order when passed around.
 """

@@ -20,7 +20,7 @@ STEV_OK, STEV_EINVAL, STEV_ENOMEM, STEV_ECUDA, STEV_ETIMEOUT, STEV_EUNBALANCED, 
     STEV_EINCOMPLETE = range(7)
 CELL_OK, CELL_MAXITER, CELL_NONFINITE, CELL_TRANGE = range(4)
 FP64, MIXED = 0, 1
-THERMO_POLY, THERMO_MLP = 0, 1
+THERMO_POLY, THERMO_MLP, THERMO_MLP_CPH = 0, 1, 2
 
 # every symbol include/stev.h declares
 EXPORTS = (

@@ -107,12 +107,13 @@ static stev_status check_options(const stev_options* o) {
   if (!(o->rof_min > 0.0 && o->rof_min <= 1.0)) return fail(STEV_EINVAL, "rof_min must be in (0, 1]");
   if (o->max_iters < 1) return fail(STEV_EINVAL, "max_iters must be >= 1");
   if (o->precision != STEV_FP64 && o->precision != STEV_MIXED) return fail(STEV_EINVAL, "unknown precision");
-  if (o->thermo != STEV_THERMO_POLY && o->thermo != STEV_THERMO_MLP) return fail(STEV_EINVAL, "unknown thermo mode");
+  if (o->thermo != STEV_THERMO_POLY && o->thermo != STEV_THERMO_MLP && o->thermo != STEV_THERMO_MLP_CPH)
+    return fail(STEV_EINVAL, "unknown thermo mode");
   if (o->lanes_per_cell != 0 && o->lanes_per_cell != 8 && o->lanes_per_cell != 16 &&
       o->lanes_per_cell != 32)
     return fail(STEV_EINVAL, "lanes_per_cell must be 0, 8, 16 or 32");
-  if (o->thermo == STEV_THERMO_MLP)
-    return fail(STEV_EINVAL, "thermo mode not available in this build");
+  if (o->thermo != STEV_THERMO_POLY && o->precision != STEV_MIXED)
+    return fail(STEV_EINVAL, "the thermo network is used by the mixed-precision path only");
   return STEV_OK;
 }
 
@@ -127,12 +128,13 @@ static void free_mech(stev_mechanism* m) {
 
 typedef void (*KernelFn)(Launch);
 
-static KernelFn select_kernel(int precision, int G) {
+static KernelFn select_kernel(int precision, int G, int thermo = STEV_THERMO_POLY) {
   if (precision == STEV_MIXED) {
+    if (thermo != STEV_THERMO_POLY) return stev_mixed_kernel<32, true>;
     switch (G) {
-      case 8: return stev_mixed_kernel<8>;
-      case 16: return stev_mixed_kernel<16>;
-      default: return stev_mixed_kernel<32>;
+      case 8: return stev_mixed_kernel<8, false>;
+      case 16: return stev_mixed_kernel<16, false>;
+      default: return stev_mixed_kernel<32, false>;
     }
   }
   switch (G) {
@@ -147,6 +149,7 @@ static KernelFn select_kernel(int precision, int G) {
 // fewer lanes per cell lengthen each cell's step (the tail of the variable
 // load).  FP64: cover the species and most reactions in one or two rounds.
 static int choose_group(int S, int R, const stev_options& o) {
+  if (o.thermo != STEV_THERMO_POLY) return 32;  // the network runs one cell per warp
   if (o.lanes_per_cell) return o.lanes_per_cell;
   if (S <= 8 && R <= 32) return 8;
   if (S <= 16 && R <= 64) return 16;
@@ -165,17 +168,18 @@ static stev_status configure(stev_mechanism* m) {
   const size_t tables =
       mixed ? table_smem_bytes_mixed(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n)
             : table_smem_bytes(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n);
-  const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n)
+  const bool net = m->opt.thermo != STEV_THERMO_POLY;
+  const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n, net)
                             : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
   const size_t limit = prop.sharedMemPerBlockOptin;
   if (tables + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
   int cells = (int)((limit - tables) / cell);
-  cells = std::min(cells, (mixed ? kMaxBlockMixed : kMaxBlock) / G);
+  cells = std::min(cells, (mixed ? (net ? kMaxBlockMixedNet : kMaxBlockMixed) : kMaxBlock) / G);
   const int per_warp = 32 / G;
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
   const size_t smem = tables + (size_t)cells * cell;
-  KernelFn k = select_kernel(m->opt.precision, G);
+  KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo);
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cells * G, smem));
@@ -392,6 +396,8 @@ extern "C" stev_status stev_mechanism_get_options(const stev_mechanism* m, stev_
 
 extern "C" long stev_resident_slots(const stev_mechanism* m) { return m ? (long)m->nslots : 0; }
 
+static MlpInfer mlp_infer_view(const stev_mechanism* m);
+
 static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   Launch L{};
   L.S = m->S;
@@ -422,6 +428,11 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   L.n_cells = n;
   L.dt = dt;
   L.counter = m->d_counter;
+  if (m->opt.thermo != STEV_THERMO_POLY && m->mlp_ready) {
+    L.mlp = mlp_infer_view(m);
+    L.mlp_h = m->opt.thermo == STEV_THERMO_MLP_CPH;
+    L.mlp_needed = ((L.mlp_h ? 2 : 1) * m->S + 7) / 8 * 8;
+  }
   return L;
 }
 
@@ -429,6 +440,8 @@ static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, co
                                     const void* Y, double dt, const void* To, const void* Yo,
                                     const void* it, const void* cs) {
   if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (m->opt.thermo != STEV_THERMO_POLY && !m->mlp_ready)
+    return fail(STEV_EINVAL, "thermo = MLP needs a trained network (stev_mlp_train or stev_mlp_set_params)");
   if (n < 0) return fail(STEV_EINVAL, "n_cells < 0");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(STEV_EINVAL, "dt_cfd must be finite and > 0");
   if (n > 0 && (!T || !P || !Y || !To || !Yo || !it || !cs)) return fail(STEV_EINVAL, "NULL array");
@@ -440,7 +453,7 @@ static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, co
 
 static stev_status launch_persistent(stev_mechanism* m, const Launch& L, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned long long), s));
-  select_kernel(m->opt.precision, m->G)<<<m->grid, m->block, m->smem, s>>>(L);
+  select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<m->grid, m->block, m->smem, s>>>(L);
   CUDA_TRY(cudaGetLastError());
   return STEV_OK;
 }
@@ -550,6 +563,8 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
   if (n == 0) return STEV_OK;
   if (!T || !P || !Y || !T_out || !Y_out || !iters || !cell_status)
     return fail(STEV_EINVAL, "NULL array");
+  if (m->opt.thermo != STEV_THERMO_POLY && !m->mlp_ready)
+    return fail(STEV_EINVAL, "thermo = MLP needs a trained network (stev_mlp_train or stev_mlp_set_params)");
   if (noalloc_bytes(n, m->S) > kNoAllocBytes) {
     long lo = 0, hi = n;  // noalloc_bytes(lo) fits, noalloc_bytes(hi) does not
     while (hi - lo > 1) {
@@ -599,7 +614,7 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
   L.T_out = dTo; L.Y_out = dYo; L.iters = dit; L.status = dst;
   L.y_soa = 0;
   L.counter = counter;
-  select_kernel(m->opt.precision, m->G)<<<m->grid, m->block, m->smem, s>>>(L);
+  select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<m->grid, m->block, m->smem, s>>>(L);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(T_out, dTo, nn * 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(Y_out, dYo, nn * m->S * 8, cudaMemcpyDeviceToHost, s));

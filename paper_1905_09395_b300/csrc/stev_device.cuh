@@ -17,6 +17,7 @@
 //              order as a reaction-major scatter would add into it.
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 
 namespace stev {
@@ -30,6 +31,7 @@ constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
 constexpr int kNone = 0xFF;
 constexpr int kMaxBlock = 512;       // threads per CTA of the FP64 persistent kernel
 constexpr int kMaxBlockMixed = 768;  // threads per CTA of the mixed persistent kernel
+constexpr int kMaxBlockMixedNet = 640;  // ... with the thermo network (more registers)
 
 enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
@@ -45,6 +47,22 @@ enum { BF_A0 = 0, BF_A1, BF_A2, BF_A3, BF_A4, BF_A5, BF_H1, BF_H2, BF_H3, BF_H4,
 __host__ __device__ inline int gather_pack(int r, int nu) { return r * 16 + (nu + 8); }
 __constant__ double kNuOf[16] = {0, 0, 0, 0, 0, 0, -2.0, -1.0, 0, 1.0, 2.0, 0, 0, 0, 0, 0};
 __constant__ float kNuOfF[16] = {0, 0, 0, 0, 0, 0, -2.0f, -1.0f, 0, 1.0f, 2.0f, 0, 0, 0, 0, 0};
+
+// Inference weights: W2 and W3 rows in BF16 (row-major [out][in]: a row of W
+// is a column of the MMA's B operand, so B fragments are direct 32-bit loads),
+// W1, b1, b2, b3, mean, std in FP32.
+struct MlpInfer {
+  const __nv_bfloat16* W2;  // [64][64]
+  const __nv_bfloat16* W3;  // [n_out][64]
+  const float* W1;          // [64]
+  const float* b1;          // [64]
+  const float* b2;          // [64]
+  const float* b3;          // [n_out]
+  const float* mean;        // [n_out]
+  const float* stdv;        // [n_out]
+  int n_out;                // padded to a multiple of 8
+  int n_valid;              // 3S: columns written to the caller's array
+};
 
 // Everything a launch needs, passed by value.
 struct Launch {
@@ -76,7 +94,12 @@ struct Launch {
   unsigned char* status;  // [n]
   int y_soa;
   unsigned long long* counter;  // next unclaimed cell
+  MlpInfer mlp;           // thermo network (mixed kernel, thermo = MLP)
+  int mlp_needed;         // network outputs the solver reads (cp/R [, H/R]), rounded up to 8
+  int mlp_h;              // 1: H/RT from the network as well
 };
+
+constexpr double kMlpTLow = 300.0, kMlpTHigh = 3000.0;  // network's training range (K)
 
 // Shared-memory footprint of the tables (bytes, 16-byte aligned).
 __host__ __device__ inline size_t table_smem_bytes(int S, int R, int n_gather, int n_hi_bins,
@@ -103,9 +126,12 @@ __host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gat
 
 // Mixed kernel cell: Y in FP64 and G/RT log2 e as a float pair (8 bytes each
 // per species); C, H/RT, a float copy of Y (S each), rates (R), history
-// [N][Rrev] and rOF (Rrev) in FP32.
-__host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n) {
+// [N][Rrev] and rOF (Rrev) in FP32; with the thermo network also 64 BF16 of
+// its layer-1 output and its 2S (rounded up to 8) outputs.
+__host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n,
+                                                       bool mlp = false) {
   size_t b = (size_t)16 * S + ((size_t)3 * S + R + (size_t)dft_n * Rrev + Rrev) * 4;
+  if (mlp) b += 64 * 2 + (size_t)((2 * S + 7) / 8 * 8) * 4;
   return (b + 15) & ~(size_t)15;
 }
 

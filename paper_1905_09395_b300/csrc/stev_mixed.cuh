@@ -18,6 +18,7 @@
 //         ringing history and DFT test (Eqs. 8-13).
 #pragma once
 #include "stev_common.cuh"
+#include "stev_mlp.cuh"
 
 namespace stev {
 
@@ -61,13 +62,22 @@ __device__ __forceinline__ double log1p_small(double u) {
   return c * u;
 }
 
-template <int G>
+// MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
+// (Sec. 3), evaluated by the cell's warp (G == 32) into cTh (cp/R, then H/R),
+// whenever T is inside the network's training range; outside it, and for G/RT
+// always, the NASA-7 polynomials are used.
+template <int G, bool MLP>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
                                           float* cYf, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
-                                          CellState& st) {
+                                          CellState& st, __nv_bfloat16* a1buf, float* cTh) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
+  bool use_net = false;
+  if (MLP) {
+    use_net = T >= kMlpTLow && T <= kMlpTHigh;  // warp-uniform: one cell per warp
+    if (use_net) mlp_eval_row(L.mlp, ((float)T - kTMid) / kTHalf, a1buf, cTh, L.mlp_needed);
+  }
   const double lnT = st.lnT;        // FP64: feeds G/RT
   const double invT = 1.0 / T;
   const float Tf = (float)T;
@@ -89,10 +99,19 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const float* b = spf + (lo ? SPF_LOW : SPF_HIGH);
     const double* bd = sp + (lo ? SP_LOW : SP_HIGH);
     const float Yi = cYf[i];
-    const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf, b[BF_A1]), Tf,
-                           b[BF_A0]);
-    const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
-    cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+    float cpR;
+    if (MLP && use_net) {
+      cpR = cTh[i];
+    } else {
+      cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf, b[BF_A1]), Tf,
+                 b[BF_A0]);
+    }
+    if (MLP && use_net && L.mlp_h) {
+      cH[i] = cTh[S + i] * invTf;  // the network gives H/R
+    } else {
+      const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
+      cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+    }
     const double gp = fma(fma(fma(bd[B_G4], T, bd[B_G3]), T, bd[B_G2]), T, bd[B_H1]);
     const double g2 = (fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T) * kLog2e;
     const float ghi = (float)g2;
@@ -252,8 +271,9 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   return -1;
 }
 
-template <int G>
-__global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
+template <int G, bool MLP>
+__global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
+    stev_mixed_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = L.S, R = L.R;
   double* s_sp = reinterpret_cast<double*>(smem_raw);
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
   const int group = threadIdx.x / G;
   const int l = threadIdx.x % G;
   const size_t tables = table_smem_bytes_mixed(S, R, L.n_gather, L.n_hi_bins, L.dft_n);
-  const size_t cell_bytes = cell_smem_bytes_mixed(S, R, L.Rrev, L.dft_n);
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, R, L.Rrev, L.dft_n, MLP);
   unsigned char* base = smem_raw + tables + (size_t)group * cell_bytes;
   double* cY = reinterpret_cast<double*>(base);
   float2* cG2 = reinterpret_cast<float2*>(cY + S);
@@ -286,6 +306,9 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
   float* cQ = cYf + S;
   float* cHist = cQ + R;
   float* cRof = cHist + L.dft_n * L.Rrev;
+  // thermo network buffers (MLP only): 64 BF16 of layer-1 output, 2S outputs
+  __nv_bfloat16* a1buf = reinterpret_cast<__nv_bfloat16*>(cRof + L.Rrev);
+  float* cTh = reinterpret_cast<float*>(a1buf + kHid);
   for (int i = l; i < S; i += G) {
     cY[i] = 0.0;
     cYf[i] = 0.0f;
@@ -322,7 +345,8 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
     }
     __syncwarp();
     if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
-    const int outcome = step_mixed<G>(L, tb, cY, cYf, cG2, cC, cH, cQ, cHist, cRof, Pf, l, st);
+    const int outcome =
+        step_mixed<G, MLP>(L, tb, cY, cYf, cG2, cC, cH, cQ, cHist, cRof, Pf, l, st, a1buf, cTh);
     if (st.cell >= 0 && outcome >= 0) {
       const long long c = st.cell;
       if (l == 0) {

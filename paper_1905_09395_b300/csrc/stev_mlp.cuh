@@ -3,7 +3,7 @@
 //
 // Network: t = (T - 1650)/1350, a1 = tanh(W1 t + b1) [64],
 // a2 = tanh(W2 a1 + b2) [64], y = W3 a2 + b3 [3S] standardised outputs
-// (cp/R of every species, then H/RT, then S/R), value = y * std + mean.
+// (cp/R of every species, then H/R in K, then S/R), value = y * std + mean.
 // Parameters are one flat FP32 array in the order W1[64], b1[64], W2[64][64],
 // b2[64], W3[3S][64], b3[3S] (rows = outputs).
 //
@@ -43,7 +43,9 @@ __host__ __device__ inline MlpOffsets mlp_offsets(int n_out) {
 
 // ----------------------------------------------------- training targets
 // NASA-7 properties (Eqs. 15-16, S/R = H/RT - G/RT) of every species at every
-// sample temperature, in FP64, stored as float: out[s][o], o = i, S+i, 2S+i.
+// sample temperature, in FP64, stored as float: out[s][o], o = i (cp/R),
+// S+i (H/R = H/RT * T, in K: smooth over the range, unlike H/RT whose a6/T
+// term grows steeply at low T), 2S+i (S/R).
 __global__ void mlp_targets_kernel(const double* __restrict__ sp_tab, int S,
                                    const double* __restrict__ T, long long n,
                                    float* __restrict__ out) {
@@ -62,7 +64,7 @@ __global__ void mlp_targets_kernel(const double* __restrict__ sp_tab, int S,
   const double gRT = fma(b[B_A0], 1.0 - lnT, fma(b[B_A5], invT, -b[B_A6])) - gp * t;
   float* o = out + s * (3 * S);
   o[i] = (float)cpR;
-  o[S + i] = (float)hRT;
+  o[S + i] = (float)(hRT * t);
   o[2 * S + i] = (float)(hRT - gRT);
 }
 
@@ -205,22 +207,6 @@ __global__ void mlp_adam_kernel(float* __restrict__ p, float* __restrict__ g,
 }
 
 // ------------------------------------------------------------- inference
-// Inference weights: W2 and W3 rows in BF16 (row-major [out][in]: a row of W
-// is a column of the MMA's B operand, so B fragments are direct 32-bit loads),
-// W1, b1, b2, b3, mean, std in FP32.
-struct MlpInfer {
-  const __nv_bfloat16* W2;  // [64][64]
-  const __nv_bfloat16* W3;  // [n_out][64]
-  const float* W1;          // [64]
-  const float* b1;          // [64]
-  const float* b2;          // [64]
-  const float* b3;          // [n_out]
-  const float* mean;        // [n_out]
-  const float* stdv;        // [n_out]
-  int n_out;                // padded to a multiple of 8
-  int n_valid;              // 3S: columns written to the caller's array
-};
-
 __device__ __forceinline__ float tanh_approx(float x) {
   float r;
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -323,6 +309,75 @@ __device__ void mlp_eval_warp16(const MlpInfer& w, const float* t16, __nv_bfloat
     if (g + 8 < n_rows) {
       if (c0ok) out[(g + 8) * out_ld + c - o_begin] = fmaf(d[2], s0, m0);
       if (c1ok) out[(g + 8) * out_ld + c + 1 - o_begin] = fmaf(d[3], s1, m1);
+    }
+  }
+  __syncwarp();
+}
+
+// The network at one temperature per warp, for the solver: row 0 of a 16-row
+// MMA tile (the other rows are zero).  a1buf is a warp-private shared buffer
+// of 64 BF16; out receives the values of outputs [0, n_needed) (n_needed a
+// multiple of 8, at most n_out).  Layer 2's row-0 results come back in lanes
+// 0-3 exactly where layer 3's A fragment needs them, so only layer 1 passes
+// through shared memory.
+__device__ void mlp_eval_row(const MlpInfer& w, float t, __nv_bfloat16* a1buf, float* out,
+                             int n_needed) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  {
+    const int j = lane * 2;
+    const float h0 = tanh_approx(fmaf(w.W1[j], t, w.b1[j]));
+    const float h1 = tanh_approx(fmaf(w.W1[j + 1], t, w.b1[j + 1]));
+    *reinterpret_cast<unsigned*>(a1buf + j) = pack_bf16(h0, h1);
+  }
+  __syncwarp();
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    acc[nt][0] = w.b2[nt * 8 + tg * 2];
+    acc[nt][1] = w.b2[nt * 8 + tg * 2 + 1];
+    acc[nt][2] = 0.0f;
+    acc[nt][3] = 0.0f;
+  }
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    unsigned a[4];
+    a[0] = g == 0 ? *reinterpret_cast<const unsigned*>(a1buf + ks * 16 + tg * 2) : 0u;
+    a[1] = 0u;
+    a[2] = g == 0 ? *reinterpret_cast<const unsigned*>(a1buf + ks * 16 + 8 + tg * 2) : 0u;
+    a[3] = 0u;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const __nv_bfloat16* wr = w.W2 + (nt * 8 + g) * kHid + ks * 16 + tg * 2;
+      unsigned b[2];
+      b[0] = __ldg(reinterpret_cast<const unsigned*>(wr));
+      b[1] = __ldg(reinterpret_cast<const unsigned*>(wr + 8));
+      mma_bf16_16816(acc[nt], a, b);
+    }
+  }
+  unsigned a3[4][4];
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    a3[ks][0] = g == 0 ? pack_bf16(tanh_approx(acc[2 * ks][0]), tanh_approx(acc[2 * ks][1])) : 0u;
+    a3[ks][1] = 0u;
+    a3[ks][2] = g == 0 ? pack_bf16(tanh_approx(acc[2 * ks + 1][0]), tanh_approx(acc[2 * ks + 1][1]))
+                       : 0u;
+    a3[ks][3] = 0u;
+  }
+  for (int o0 = 0; o0 < n_needed; o0 += 8) {
+    const int c = o0 + tg * 2;
+    float d[4] = {w.b3[c], w.b3[c + 1], 0.0f, 0.0f};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const __nv_bfloat16* wr = w.W3 + (o0 + g) * kHid + ks * 16 + tg * 2;
+      unsigned b[2];
+      b[0] = __ldg(reinterpret_cast<const unsigned*>(wr));
+      b[1] = __ldg(reinterpret_cast<const unsigned*>(wr + 8));
+      mma_bf16_16816(d, a3[ks], b);
+    }
+    if (g == 0) {
+      out[c] = fmaf(d[0], w.stdv[c], w.mean[c]);
+      out[c + 1] = fmaf(d[1], w.stdv[c + 1], w.mean[c + 1]);
     }
   }
   __syncwarp();

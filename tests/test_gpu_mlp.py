@@ -78,8 +78,9 @@ def test_accuracy_against_polynomials(trained):
     T = np.random.default_rng(5).uniform(300.0, 3000.0, size=4000)
     got = m.mlp_eval(torch.from_numpy(T).cuda()).cpu().numpy()
     want = np.array([np.concatenate(oracle.thermo(mech, t)) for t in T])
+    want[:, S:2 * S] *= T[:, None]           # the network's second block is H/R (K)
     cp_rel = np.abs(got[:, :S] - want[:, :S]) / np.abs(want[:, :S])
-    h_abs = np.abs(got[:, S:2 * S] - want[:, S:2 * S])
+    h_abs = np.abs(got[:, S:2 * S] - want[:, S:2 * S]) / T[:, None]   # back to H/RT units
     s_abs = np.abs(got[:, 2 * S:] - want[:, 2 * S:])
     print("cp/R relative error: max %.3f%%, mean %.3f%%; H/RT abs max %.3g mean %.3g;"
           " S/R abs max %.3g mean %.3g" % (100 * cp_rel.max(), 100 * cp_rel.mean(), h_abs.max(),
