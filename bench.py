@@ -3,8 +3,10 @@
 One step = one stev_solve of every cell of the workload (32 species / 150
 reactions, T0 U[800,2200] K, P U[1,5] atm, Y0 Dirichlet(0.5), dt = 1e-3 s),
 i.e. one pass of the whole hot path over one batch.  The line's value is the
-mixed-precision path; the plain FP64 path is timed once on the same cells
-beside it ("plain_fp64").  Warm-up solves run the same kernel and launch
+mixed-precision path with cp/R from the thermo network ("mixed+MLP", the
+network trained on the GPU before the timed region); the same cells are
+timed once with the polynomial thermo ("mixed_poly") and once on the plain
+FP64 path ("plain_fp64").  Warm-up solves run the same kernel and launch
 configuration on the first --warmup-cells cells.  Cells are independent,
 so with N GPUs every rank solves its own batch (weak scaling, no collective on
 the data path; a barrier only brackets the timed region).
@@ -44,7 +46,7 @@ FP64_PEAK_OPS = 4.733e11
 # profiles/ (3,108- and 1,628-cell cases; reads only: the small cases' output
 # writes stay in L2), scaled to the full launch by the cells it processes.
 # Set to None when the kernel changes after the capture.
-DRAM_BYTES_PER_CELL = {"mixed": 924160 / 3108, "fp64": 528896 / 1628}
+DRAM_BYTES_PER_CELL = {"mixed": 924160 / 3108, "fp64": 528896 / 1628, "mixed+mlp": None}
 
 
 def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
@@ -239,9 +241,9 @@ def run_ours(args):
     prec = binding.MIXED if args.precision == "mixed" else binding.FP64
     m = Mechanism(mech, precision=prec, **extra)
     mlp_info = None
+    if args.precision != "mixed":
+        args.thermo = "poly"
     if args.thermo == "mlp":
-        if args.precision != "mixed":
-            raise SystemExit("--thermo mlp needs --precision mixed")
         t0 = time.time()
         Ts = np.random.default_rng(2024).uniform(300.0, 3000.0, size=args.mlp_samples)
         hist = m.mlp_train(Ts, epochs=args.mlp_epochs, batch=4096, lr=2e-3, seed=7)
@@ -300,26 +302,34 @@ def run_ours(args):
                "d2h_bytes_per_step": int(sum(x.nbytes for x in ho)), "steps": ke}
     m.close()
 
-    # the plain FP64 path on the same cells, for the mixed-vs-FP64 comparison
-    plain = None
+    def one_solve(mc, ops):
+        """One timed solve of the same cells by another configuration."""
+        msx, _, _ = timed_solves(mc, Td, Pd, Yd, dt, out, 1, args.warmup, args.warmup_cells,
+                                 stream, dist)
+        itx = out[2].cpu().numpy().astype(np.int64)
+        tx = msx[0] / 1e3
+        if dist is not None:
+            t = torch.tensor([tx], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tx = float(t.item())
+        ach = ops * int(itx.sum()) / (msx[0] / 1e3)
+        return {"value": n * world / tx, "unit": UNIT, "ms_per_step": tx * 1e3, "steps": 1,
+                "warmup": args.warmup, "cell_steps_per_s": int(itx.sum()) / tx,
+                "roofline": {"bound": "alu", "achieved": 2 * ach / 1e12,
+                             "peak": 2 * FP64_PEAK_OPS / 1e12, "unit": "TFLOP/s",
+                             "frac": ach / FP64_PEAK_OPS, "traffic": None,
+                             "ops_per_cell_step": ops}}
+
+    # the same cells with the polynomial thermo (what the network gains) and
+    # with the plain FP64 path (what mixed precision gains)
+    mixed_poly, plain = None, None
+    if args.precision == "mixed" and args.thermo == "mlp" and not args.no_poly_compare:
+        mp = Mechanism(mech, precision=binding.MIXED, **extra)
+        mixed_poly = one_solve(mp, mixed_fp64_ops_per_cell_step(S))
+        mp.close()
     if args.precision == "mixed" and not args.no_fp64_compare:
         mf = Mechanism(mech, precision=binding.FP64, **extra)
-        msf, wallf, _ = timed_solves(mf, Td, Pd, Yd, dt, out, 1, args.warmup,
-                                     args.warmup_cells, stream, dist)
-        itf = out[2].cpu().numpy().astype(np.int64)
-        tf = msf[0] / 1e3
-        if dist is not None:
-            t = torch.tensor([tf], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tf = float(t.item())
-        opsf = fp64_ops_per_cell_step(S, R, Rrev, nnz)
-        achf = opsf * int(itf.sum()) / (msf[0] / 1e3)
-        plain = {"value": n * world / tf, "unit": UNIT, "ms_per_step": tf * 1e3, "steps": 1,
-                 "warmup": args.warmup, "cell_steps_per_s": int(itf.sum()) / tf,
-                 "roofline": {"bound": "alu", "achieved": 2 * achf / 1e12,
-                              "peak": 2 * FP64_PEAK_OPS / 1e12, "unit": "TFLOP/s",
-                              "frac": achf / FP64_PEAK_OPS, "traffic": None,
-                              "ops_per_cell_step": opsf}}
+        plain = one_solve(mf, fp64_ops_per_cell_step(S, R, Rrev, nnz))
         mf.close()
 
     if rank != 0:
@@ -333,7 +343,7 @@ def run_ours(args):
         ops_note = ("the method's FP64 work: exp = %g, log = %g, div = %g DFMA-equivalents, "
                     "measured" % (EXP_OPS, LOG_OPS, DIV_OPS))
     achieved = ops * cell_steps / (float(np.mean(ms)) / 1e3)
-    bpc = DRAM_BYTES_PER_CELL.get(args.precision)
+    bpc = DRAM_BYTES_PER_CELL.get(args.precision + ("+mlp" if args.thermo == "mlp" else ""))
     roofline = {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * FP64_PEAK_OPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_OPS,
                 "traffic": None if bpc is None else bpc * n,
@@ -363,7 +373,8 @@ def run_ours(args):
             "cell_status": {"ok": int(status[0]), "maxiter": int(status[1]),
                             "nonfinite": int(status[2]), "trange": int(status[3])},
             "roofline": roofline, "gpu_launches": args.steps, "e2e": e2e,
-            "plain_fp64": plain, "thermo_net": mlp_info, "wall_s_timed": wall}
+            "mixed_poly": mixed_poly, "plain_fp64": plain, "thermo_net": mlp_info,
+            "wall_s_timed": wall}
     line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **extra)
@@ -378,7 +389,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--thermo", choices=["poly", "mlp"], default="poly")
+    ap.add_argument("--thermo", choices=["poly", "mlp"], default="mlp",
+                    help="mlp: cp/R from the thermo network trained before timing (mixed only)")
+    ap.add_argument("--no-poly-compare", action="store_true",
+                    help="skip the polynomial-thermo mixed solve of the same cells")
     ap.add_argument("--mlp-samples", type=int, default=1_000_000)
     ap.add_argument("--mlp-epochs", type=int, default=30)
     ap.add_argument("--no-fp64-compare", action="store_true",

@@ -131,6 +131,20 @@ stev_status stev_solve_soa(stev_mechanism *mech, long n_cells, const double *T, 
                            const double *Y_soa, double dt_cfd, double *T_out, double *Y_out_soa,
                            int *iters, unsigned char *cell_status, void *cuda_stream);
 
+/* Integrates n_batches independent batches of cells in ONE persistent launch
+ * (Sec. 2.4's variable load across all of them): batch b has n_cells[b]
+ * cells, its own fluid time step dt[b] and its own DEVICE arrays T[b], P[b],
+ * Y[b] ([n][S]), T_out[b], Y_out[b], iters[b], cell_status[b]; the pointer
+ * arrays and n_cells, dt are HOST arrays.  Batches of 0 cells are skipped.
+ * Each cell's result equals the one stev_solve gives it.  The batch table is
+ * copied to a device buffer the mechanism owns (grown when n_batches grows).
+ * Asynchronous on cuda_stream. */
+stev_status stev_solve_batched(stev_mechanism *mech, int n_batches, const long *n_cells,
+                               const double *const *T, const double *const *P,
+                               const double *const *Y, const double *dt, double *const *T_out,
+                               double *const *Y_out, int *const *iters,
+                               unsigned char *const *cell_status, void *cuda_stream);
+
 /* As stev_solve with HOST arrays: copies the inputs to the device, solves and
  * copies the results back on cuda_stream, then waits for the stream.
  * Device buffers are owned by the mechanism and reused across calls. */

@@ -28,7 +28,7 @@ EXPORTS = (
     "stev_mechanism_get_options", "stev_solve", "stev_solve_soa", "stev_solve_host",
     "stev_resident_slots", "stev_destroy", "stev_last_error", "stev_solve_host_noalloc",
     "stev_mlp_num_params", "stev_mlp_train", "stev_mlp_set_params", "stev_mlp_get_params",
-    "stev_mlp_loss_grad", "stev_mlp_eval",
+    "stev_mlp_loss_grad", "stev_mlp_eval", "stev_solve_batched",
 )
 
 
@@ -88,6 +88,8 @@ def lib():
         L.stev_mlp_loss_grad.restype = I
         L.stev_mlp_eval.argtypes = [P, P, LNG, P, P]
         L.stev_mlp_eval.restype = I
+        L.stev_solve_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P]
+        L.stev_solve_batched.restype = I
         L.stev_resident_slots.argtypes = [P]
         L.stev_resident_slots.restype = LNG
         L.stev_destroy.argtypes = [P]
@@ -195,6 +197,33 @@ class Mechanism:
         _check(fn(self._h, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(), float(dt), To.data_ptr(),
                   Yo.data_ptr(), it.data_ptr(), st.data_ptr(), _stream_handle(stream)))
         return To, Yo, it, st
+
+    def solve_batched(self, batches, dt, stream=None):
+        """Independent batches in one launch (stev_solve_batched).
+
+        batches: list of (T, P, Y) CUDA tensors; dt: one float or one per batch.
+        Returns a list of (T_out, Y_out, iters, status) per batch."""
+        import torch
+        nb = len(batches)
+        dts = np.full(nb, float(dt)) if np.isscalar(dt) else _np(dt, np.float64)
+        outs, keep = [], []
+        arr = lambda vals: (ctypes.c_void_p * max(nb, 1))(*vals)
+        ptrs = {k: [] for k in ("T", "P", "Y", "To", "Yo", "it", "st")}
+        sizes = np.zeros(nb, dtype=np.int64)
+        for b, (T, P, Y) in enumerate(batches):
+            n = self._check_dev(T, P, Y, False)
+            sizes[b] = n
+            o = (torch.empty_like(T), torch.empty_like(Y),
+                 torch.empty(n, dtype=torch.int32, device=T.device),
+                 torch.empty(n, dtype=torch.uint8, device=T.device))
+            outs.append(o)
+            for k, t in zip(("T", "P", "Y", "To", "Yo", "it", "st"), (T, P, Y) + o):
+                ptrs[k].append(t.data_ptr())
+        c = {k: arr(v) for k, v in ptrs.items()}
+        _check(lib().stev_solve_batched(self._h, nb, sizes.ctypes.data, c["T"], c["P"], c["Y"],
+                                        dts.ctypes.data, c["To"], c["Yo"], c["it"], c["st"],
+                                        _stream_handle(stream)))
+        return outs
 
     def solve_host(self, T, P, Y, dt: float, out=None, stream=None):
         """Host-pointer solve (stev_solve_host): numpy in, numpy out, blocking."""

@@ -67,6 +67,10 @@ struct stev_mechanism {
   int* d_hit = nullptr;
   unsigned char* d_hst = nullptr;
   long long host_cap = 0;
+  // batch descriptors of stev_solve_batched: [cap] BatchDesc + [cap+1] offsets
+  BatchDesc* d_bdesc = nullptr;
+  long long* d_boff = nullptr;
+  int batch_cap = 0;
   // thermo network (Sec. 3)
   int mlp_out = 0, mlp_out_pad = 0, mlp_np = 0;
   float* d_mlp_params = nullptr;          // FP32 master parameters
@@ -120,6 +124,7 @@ static stev_status check_options(const stev_options* o) {
 static void free_mech(stev_mechanism* m) {
   void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
                   m->d_twf, m->d_counter, m->d_mlp_params, m->d_mlp_W2, m->d_mlp_W3, m->d_mlp_misc,
+                  m->d_bdesc, m->d_boff,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -481,6 +486,62 @@ extern "C" stev_status stev_solve_soa(stev_mechanism* m, long n, const double* T
                                       const double* Y, double dt, double* T_out, double* Y_out,
                                       int* iters, unsigned char* cell_status, void* stream) {
   return solve_impl(m, n, T, P, Y, dt, T_out, Y_out, iters, cell_status, stream, 1);
+}
+
+extern "C" stev_status stev_solve_batched(stev_mechanism* m, int n_batches, const long* n_cells,
+                                          const double* const* T, const double* const* P,
+                                          const double* const* Y, const double* dt,
+                                          double* const* T_out, double* const* Y_out,
+                                          int* const* iters, unsigned char* const* cell_status,
+                                          void* stream) {
+  g_err.clear();
+  if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (n_batches < 0) return fail(STEV_EINVAL, "n_batches < 0");
+  if (n_batches == 0) return STEV_OK;
+  if (!n_cells || !T || !P || !Y || !dt || !T_out || !Y_out || !iters || !cell_status)
+    return fail(STEV_EINVAL, "NULL argument");
+  std::vector<BatchDesc> desc;
+  std::vector<long long> off(1, 0);
+  for (int b = 0; b < n_batches; ++b) {
+    if (n_cells[b] < 0) return fail(STEV_EINVAL, "n_cells[%d] < 0", b);
+    if (n_cells[b] == 0) continue;
+    if (!(dt[b] > 0.0) || !std::isfinite(dt[b])) return fail(STEV_EINVAL, "dt[%d] must be finite and > 0", b);
+    if (!T[b] || !P[b] || !Y[b] || !T_out[b] || !Y_out[b] || !iters[b] || !cell_status[b])
+      return fail(STEV_EINVAL, "NULL array in batch %d", b);
+    BatchDesc d;
+    d.T = T[b]; d.P = P[b]; d.Y = Y[b]; d.T_out = T_out[b]; d.Y_out = Y_out[b];
+    d.iters = iters[b]; d.status = cell_status[b]; d.dt = dt[b]; d.n = n_cells[b];
+    desc.push_back(d);
+    off.push_back(off.back() + n_cells[b]);
+  }
+  if (desc.empty()) return STEV_OK;
+  stev_status st = check_solve_args(m, (long)off.back(), desc[0].T, desc[0].P, desc[0].Y, desc[0].dt,
+                                    desc[0].T_out, desc[0].Y_out, desc[0].iters, desc[0].status);
+  if (st != STEV_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)desc.size();
+  if (nb > m->batch_cap) {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (m->d_bdesc) cudaFree(m->d_bdesc);
+    if (m->d_boff) cudaFree(m->d_boff);
+    m->d_bdesc = nullptr;
+    m->d_boff = nullptr;
+    m->batch_cap = 0;
+    CUDA_TRY(cudaMalloc(&m->d_bdesc, (size_t)nb * sizeof(BatchDesc)));
+    CUDA_TRY(cudaMalloc(&m->d_boff, (size_t)(nb + 1) * sizeof(long long)));
+    m->batch_cap = nb;
+  }
+  // pageable sources: the copies are staged before cudaMemcpyAsync returns
+  CUDA_TRY(cudaMemcpyAsync(m->d_bdesc, desc.data(), desc.size() * sizeof(BatchDesc),
+                           cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(m->d_boff, off.data(), off.size() * sizeof(long long),
+                           cudaMemcpyHostToDevice, s));
+  Launch L = make_launch(m, off.back(), desc[0].dt);
+  L.nb = nb;
+  L.boff = m->d_boff;
+  L.bdesc = m->d_bdesc;
+  L.y_soa = 0;
+  return launch_persistent(m, L, s);
 }
 
 extern "C" stev_status stev_solve_host(stev_mechanism* m, long n, const double* T, const double* P,

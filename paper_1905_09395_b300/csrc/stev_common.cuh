@@ -41,7 +41,47 @@ struct CellState {
   int it;
   int nhist;
   double lnT;       // mixed kernel: ln T kept up to date incrementally
+  double dt;        // this cell's fluid time step t_f
+  long long lc;     // index inside its batch
+  int b;            // its batch (batched launches)
 };
+
+// Where cell c's arrays are: resolves batched launches by binary search over
+// the batch offsets (every batch non-empty).
+struct CellIO {
+  const double* T;
+  const double* P;
+  const double* Y;
+  double* T_out;
+  double* Y_out;
+  int* iters;
+  unsigned char* status;
+  double dt;
+  long long n;   // cells in the batch (the Y stride of species-major input)
+};
+
+__device__ __forceinline__ CellIO cell_io(const Launch& L, int b) {
+  CellIO io;
+  if (L.nb > 0) {
+    const BatchDesc& d = L.bdesc[b];
+    io.T = d.T; io.P = d.P; io.Y = d.Y; io.T_out = d.T_out; io.Y_out = d.Y_out;
+    io.iters = d.iters; io.status = d.status; io.dt = d.dt; io.n = d.n;
+  } else {
+    io.T = L.T; io.P = L.P; io.Y = L.Y; io.T_out = L.T_out; io.Y_out = L.Y_out;
+    io.iters = L.iters; io.status = L.status; io.dt = L.dt; io.n = L.n_cells;
+  }
+  return io;
+}
+
+__device__ __forceinline__ int find_batch(const Launch& L, long long c) {
+  if (L.nb <= 0) return 0;
+  int lo = 0, hi = L.nb;  // boff[lo] <= c < boff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (L.boff[mid] <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 struct Tables {
   const double* sp;

@@ -64,6 +64,20 @@ struct MlpInfer {
   int n_valid;              // 3S: columns written to the caller's array
 };
 
+// One independent batch of cells in a batched launch (its own arrays, size
+// and fluid time step).  Layouts as for the single-batch entry points.
+struct BatchDesc {
+  const double* T;
+  const double* P;
+  const double* Y;        // [n][S]
+  double* T_out;
+  double* Y_out;          // [n][S]
+  int* iters;
+  unsigned char* status;
+  double dt;
+  long long n;
+};
+
 // Everything a launch needs, passed by value.
 struct Launch {
   // mechanism
@@ -94,6 +108,11 @@ struct Launch {
   unsigned char* status;  // [n]
   int y_soa;
   unsigned long long* counter;  // next unclaimed cell
+  // batched launches: nb > 0 batches, cell id c belongs to the batch b with
+  // boff[b] <= c < boff[b+1]; the single-batch fields above are then unused
+  int nb;
+  const long long* boff;  // [nb+1]
+  const BatchDesc* bdesc; // [nb]
   MlpInfer mlp;           // thermo network (mixed kernel, thermo = MLP)
   int mlp_needed;         // network outputs the solver reads (cp/R [, H/R]), rounded up to 8
   int mlp_h;              // 1: H/RT from the network as well

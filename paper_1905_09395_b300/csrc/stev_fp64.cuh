@@ -113,7 +113,7 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
   const double hw = group_sum<G>(hwp);
   group_min_frac<G>(num, den);
   const double dTdt = -(T * hw) / (rho * cpsum);
-  double h = fmin(num / den, L.dt * L.delta_max);
+  double h = fmin(num / den, st.dt * L.delta_max);
   const bool last = (h >= st.t_rem);
   if (last) h = st.t_rem;
 
@@ -224,38 +224,47 @@ __global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
   st.T = 1000.0;
   st.P = kPatm;
   st.t_rem = 1.0;
+  st.dt = 1.0;
+  st.lc = 0;
+  st.b = 0;
   st.it = 0;
   st.nhist = 0;
   bool exhausted = false;  // warp-uniform
   while (true) {
     const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
     if (c >= 0) {
+      st.b = find_batch(L, c);
+      const CellIO io = cell_io(L, st.b);
+      st.lc = L.nb > 0 ? c - L.boff[st.b] : c;
+      const long long lc = st.lc;
       st.cell = c;
-      st.T = L.T[c];
-      st.P = L.P[c];
-      st.t_rem = L.dt;
+      st.T = io.T[lc];
+      st.P = io.P[lc];
+      st.dt = io.dt;
+      st.t_rem = io.dt;
       st.it = 0;
       st.nhist = 0;
       if (L.y_soa)
-        for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
+        for (int i = l; i < S; i += G) cY[i] = io.Y[(long long)i * io.n + lc];
       else
-        for (int i = l; i < S; i += G) cY[i] = L.Y[c * S + i];
+        for (int i = l; i < S; i += G) cY[i] = io.Y[lc * S + i];
       for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0;  // Eq. 11
     }
     __syncwarp();
     if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
     const int outcome = step_fp64<G>(L, tb, cY, cC, cG, cH, cQ, cHist, cRof, l, st);
     if (st.cell >= 0 && outcome >= 0) {
-      const long long c = st.cell;
+      const CellIO io = cell_io(L, st.b);
+      const long long c = st.lc;
       if (l == 0) {
-        L.T_out[c] = st.T;
-        L.iters[c] = st.it;
-        L.status[c] = (unsigned char)outcome;
+        io.T_out[c] = st.T;
+        io.iters[c] = st.it;
+        io.status[c] = (unsigned char)outcome;
       }
       if (L.y_soa)
-        for (int i = l; i < S; i += G) L.Y_out[(long long)i * L.n_cells + c] = cY[i];
+        for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = cY[i];
       else
-        for (int i = l; i < S; i += G) L.Y_out[c * S + i] = cY[i];
+        for (int i = l; i < S; i += G) io.Y_out[c * S + i] = cY[i];
       st.cell = -1;
     }
   }

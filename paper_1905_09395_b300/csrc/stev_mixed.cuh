@@ -193,7 +193,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   const float hw = group_sum<G>(hwp);
   tmin = group_min<G>(tmin);
   const float dTdt = -(Tf * hw) / (rho * cpsum);
-  double h = fmin((double)tmin, L.dt * L.delta_max);
+  double h = fmin((double)tmin, st.dt * L.delta_max);
   const bool last = (h >= st.t_rem);
   if (last) h = st.t_rem;
   const float hf = (float)h;
@@ -320,6 +320,9 @@ __global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
   st.T = 1000.0;
   st.P = kPatm;
   st.t_rem = 1.0;
+  st.dt = 1.0;
+  st.lc = 0;
+  st.b = 0;
   st.it = 0;
   st.nhist = 0;
   st.lnT = log(1000.0);
@@ -328,18 +331,23 @@ __global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
   while (true) {
     const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
     if (c >= 0) {
+      st.b = find_batch(L, c);
+      const CellIO io = cell_io(L, st.b);
+      st.lc = L.nb > 0 ? c - L.boff[st.b] : c;
+      const long long lc = st.lc;
       st.cell = c;
-      st.T = L.T[c];
-      st.P = L.P[c];
-      st.t_rem = L.dt;
+      st.T = io.T[lc];
+      st.P = io.P[lc];
+      st.dt = io.dt;
+      st.t_rem = io.dt;
       st.it = 0;
       st.nhist = 0;
       st.lnT = log(st.T);
       Pf = (float)st.P;
       if (L.y_soa)
-        for (int i = l; i < S; i += G) cY[i] = L.Y[(long long)i * L.n_cells + c];
+        for (int i = l; i < S; i += G) cY[i] = io.Y[(long long)i * io.n + lc];
       else
-        for (int i = l; i < S; i += G) cY[i] = L.Y[c * S + i];
+        for (int i = l; i < S; i += G) cY[i] = io.Y[lc * S + i];
       for (int i = l; i < S; i += G) cYf[i] = (float)cY[i];
       for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0f;
     }
@@ -348,16 +356,17 @@ __global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
     const int outcome =
         step_mixed<G, MLP>(L, tb, cY, cYf, cG2, cC, cH, cQ, cHist, cRof, Pf, l, st, a1buf, cTh);
     if (st.cell >= 0 && outcome >= 0) {
-      const long long c = st.cell;
+      const CellIO io = cell_io(L, st.b);
+      const long long c = st.lc;
       if (l == 0) {
-        L.T_out[c] = st.T;
-        L.iters[c] = st.it;
-        L.status[c] = (unsigned char)outcome;
+        io.T_out[c] = st.T;
+        io.iters[c] = st.it;
+        io.status[c] = (unsigned char)outcome;
       }
       if (L.y_soa)
-        for (int i = l; i < S; i += G) L.Y_out[(long long)i * L.n_cells + c] = cY[i];
+        for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = cY[i];
       else
-        for (int i = l; i < S; i += G) L.Y_out[c * S + i] = cY[i];
+        for (int i = l; i < S; i += G) io.Y_out[c * S + i] = cY[i];
       st.cell = -1;
     }
   }

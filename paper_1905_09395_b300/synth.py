@@ -275,9 +275,26 @@ def scale_case(n_cells: int = 1 << 20, seed: int = 1):
 
 
 def large_mechanism():
-    """53 species / 325 reactions, Ea 0-250 kJ/mol."""
-    return make_mechanism(53, 325, seed=3, ea_max=250e3, min_stiffness=1e6,
+    """53 species / 325 reactions, Ea 0-250 kJ/mol, A log-uniform 1e6-1e11
+    (cm-mol-s), stiffness ratio >= 1e6.  With A up to 1e14 nearly every cell
+    of this mechanism needs more than 2e5 STEV iterations at dt = 5e-4 s (the
+    paper reports STEV degrading on detailed mechanisms with many stiff
+    reversible reactions); 1e11 keeps cells that the method finishes."""
+    return make_mechanism(53, 325, seed=3, ea_max=250e3, a_hi=1e11, min_stiffness=1e6,
                           name="syn53x325")
+
+
+def uneven_case(scale: float = 1.0, seed: int = 3):
+    """64 independent batches, sizes log-uniform 1k-256k (times `scale`),
+    T0 U[700,2500] K, P U[1,5] atm, Y0 Dirichlet(0.5), dt = 5e-4 s, on the
+    53/325 mechanism.  Returns (mech, [(T, P, Y) per batch], dt)."""
+    mech = large_mechanism()
+    sizes = np.maximum(1, (uneven_batch_sizes(seed=seed) * scale).astype(np.int64))
+    batches = []
+    for b, n in enumerate(sizes):
+        batches.append(make_cells(mech, int(n), seed=seed * 1000 + b, T_range=(700.0, 2500.0),
+                                  P_atm_range=(1.0, 5.0), dirichlet=0.5))
+    return mech, batches, 5e-4
 
 
 def uneven_batch_sizes(n_batches: int = 64, lo: int = 1000, hi: int = 256000, seed: int = 3):
