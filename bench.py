@@ -226,6 +226,67 @@ def timed_solves(m, Td, Pd, Yd, dt, out, steps, warmup, warmup_cells, stream, di
     return [a.elapsed_time(b) for a, b in ev], wall, nw
 
 
+def run_uneven(args):
+    """Uneven independent batches (64 batches, log-uniform 1k-256k cells, the
+    53/325 mechanism, dt 5e-4 s) in ONE batched launch per step, against the
+    same batches as one stev_solve launch each."""
+    import torch
+    from paper_1905_09395_b300 import Mechanism, binding, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    mech, host_batches, dt = synth.uneven_case(args.uneven_scale)
+    extra = {} if args.max_iters is None else {"max_iters": args.max_iters}
+    m = Mechanism(mech, precision=binding.MIXED, **extra)
+    info = None
+    if args.thermo == "mlp":
+        t0 = time.time()
+        Ts = np.random.default_rng(2024).uniform(300.0, 3000.0, size=args.mlp_samples)
+        hist = m.mlp_train(Ts, epochs=args.mlp_epochs, batch=4096, lr=2e-3, seed=7)
+        m.set_options(thermo=binding.THERMO_MLP)
+        info = {"final_loss": float(hist[-1]), "train_s": time.time() - t0}
+    batches = [tuple(torch.from_numpy(a).to(dev) for a in b) for b in host_batches]
+    total = int(sum(b[0].shape[0] for b in batches))
+    # warm-up: the first batch alone, the same kernel and launch configuration
+    for _ in range(args.warmup):
+        m.solve_batched(batches[:1], dt)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            outs = m.solve_batched(batches, dt)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    iters = np.concatenate([o[2].cpu().numpy() for o in outs]).astype(np.int64)
+    status = np.bincount(np.concatenate([o[3].cpu().numpy() for o in outs]), minlength=4)
+    # the same batches as separate launches, back to back on one stream
+    e0.record()
+    for b in batches:
+        m.solve(*b, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_sep = e0.elapsed_time(e1)
+    line = {"metric": "cell-solves/s, 64 uneven batches in one persistent launch", "value":
+            total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "syn53x325, 64 batches log-uniform 1k-256k cells x %g "
+                                   "(%d cells), T0 U[700,2500] K, P U[1,5] atm, Y0 "
+                                   "Dirichlet(0.5), dt 5e-4 s" % (args.uneven_scale, total),
+                       "precision": "mixed", "thermo": args.thermo},
+            "separate_launches": {"value": total / (ms_sep / 1e3), "ms": ms_sep},
+            "cell_steps_per_s": float(iters.sum()) / (ms / 1e3),
+            "iters": {"mean": float(iters.mean()), "p50": float(np.percentile(iters, 50)),
+                      "p99": float(np.percentile(iters, 99)), "max": int(iters.max())},
+            "cell_status": {"ok": int(status[0]), "maxiter": int(status[1]),
+                            "nonfinite": int(status[2]), "trange": int(status[3])},
+            "thermo_net": info, "gpu_launches": args.steps, "clocks": clk.summary()}
+    print(json.dumps(line))
+    m.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_1905_09395_b300 import Mechanism, binding
@@ -388,6 +449,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["scale", "uneven"], default="scale",
+                    help="uneven: 64 uneven 53/325 batches in one batched launch")
+    ap.add_argument("--uneven-scale", type=float, default=1.0,
+                    help="multiplies every batch size of the uneven workload")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--thermo", choices=["poly", "mlp"], default="mlp",
                     help="mlp: cp/R from the thermo network trained before timing (mixed only)")
@@ -406,6 +471,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
     return run_ours(args)
 
 
