@@ -287,6 +287,177 @@ def run_uneven(args):
     return 0
 
 
+SERVE_BUDGET = 40 << 30  # device-memory admission budget of the serving workload
+
+
+def _serve_mechanisms(arm, args, trained=None):
+    """The 8/20 and 32/150 mechanisms for one serving arm ("mixed+mlp" or
+    "fp64"); networks trained on the GPU (or taken from `trained`)."""
+    from paper_1905_09395_b300 import Mechanism, binding, synth
+    tabs = [synth.small_mechanism(), synth.scale_mechanism()]
+    prec = binding.MIXED if arm == "mixed+mlp" else binding.FP64
+    ms = [Mechanism(t, precision=prec) for t in tabs]
+    if arm == "mixed+mlp":
+        Ts = np.random.default_rng(2024).uniform(300.0, 3000.0, size=args.mlp_samples)
+        for i, m in enumerate(ms):
+            if trained is not None and trained[i] is not None:
+                m.mlp_set_params(*trained[i])
+            else:
+                m.mlp_train(Ts, epochs=args.mlp_epochs, batch=4096, lr=2e-3, seed=7)
+            m.set_options(thermo=binding.THERMO_MLP)
+    return tabs, ms
+
+
+def serve_arm(arm, args, trained=None, rate=None, seconds=None, drain=None):
+    """One serving run: the seeded Poisson request stream (rate, duration,
+    sizes log-uniform 1k-512k, 8/20 and 32/150 mechanisms half and half) fed
+    to a stev_server with a 40 GB admission budget, every request's inputs
+    copied from pinned host memory and its results copied back.  Requests
+    still unfinished `drain` seconds after the last arrival are cancelled
+    (stev_server_stop) and counted as backlog; the cells they had solved
+    count toward the throughput."""
+    import torch
+    from paper_1905_09395_b300 import Server, synth
+    rate = args.serve_rate if rate is None else rate
+    seconds = args.serve_seconds if seconds is None else seconds
+    drain = args.serve_drain if drain is None else drain
+    hi = 512 * 1024
+    reqs = synth.serving_requests(seconds, rate, 1000, hi, 2, seed=4)
+    tabs, ms = _serve_mechanisms(arm, args, trained)
+    pools, outs = [], []
+    for i, t in enumerate(tabs):
+        T, P, Y = synth.make_cells(t, hi, seed=50 + i, T_range=(800.0, 2200.0),
+                                   P_atm_range=(1.0, 5.0), dirichlet=0.5)
+        pools.append(tuple(torch.from_numpy(a).pin_memory().numpy() for a in (T, P, Y)))
+        # one output area per mechanism, shared by its requests (results are not read)
+        outs.append((torch.empty(hi, dtype=torch.float64).pin_memory().numpy(),
+                     torch.empty((hi, t.n_species), dtype=torch.float64).pin_memory().numpy(),
+                     torch.empty(hi, dtype=torch.int32).pin_memory().numpy(),
+                     torch.empty(hi, dtype=torch.uint8).pin_memory().numpy()))
+    # SM shares in proportion to each mechanism's offered work: cells x cost per
+    # cell, the cost timed on a warm-up solve of 16,384 pool cells on all SMs
+    dev = torch.device("cuda", 0)
+    cost = []
+    for i, m in enumerate(ms):
+        Td, Pd, Yd = (torch.from_numpy(a[:16384]).to(dev) for a in pools[i])
+        for _ in range(max(1, args.warmup - 1)):
+            m.solve(Td, Pd, Yd, 1e-3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.solve(Td, Pd, Yd, 1e-3)
+        torch.cuda.synchronize()
+        cost.append((time.perf_counter() - t0) / 16384)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    work = [cost[i] * sum(r[2] for r in reqs if r[1] == i) for i in range(2)]
+    s0 = int(round(sms * work[0] / max(sum(work), 1e-30)))
+    share = [min(max(s0, 4), sms - 4)]
+    share.append(sms - share[0])
+    srv = Server(ms, sm_share=share, mem_budget=SERVE_BUDGET, queue_len=4096)
+    reports, lag, k = [], 0.0, 0
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        c0 = srv.clock()
+        while True:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k][0] <= now:
+                _, mi, n, off = reqs[k]
+                T, P, Y = pools[mi]
+                o = tuple(a[off:off + n] for a in outs[mi])
+                srv.submit(mi, T[off:off + n], P[off:off + n], Y[off:off + n], 1e-3, out=o)
+                lag = max(lag, now - reqs[k][0])
+                k += 1
+            if now >= seconds + drain:
+                break
+            if k == len(reqs) and len(reports) == len(reqs):
+                break
+            wait = 0.005 if k == len(reqs) else min(0.005, max(0.0, reqs[k][0] - now))
+            reports += srv.poll(timeout=wait)
+        srv.stop(timeout=120.0)     # cells in flight finish; nothing new starts
+        elapsed = time.perf_counter() - t0
+        while True:
+            more = srv.poll()
+            if not more:
+                break
+            reports += more
+        st = srv.stats
+    srv.close(timeout=120.0)
+    for m in ms:
+        m.close()
+    done = [d for d in reports if d["status"] == 0]
+    lat = np.array([d["t_done"] - d["t_submit"] for d in done]) if done else np.zeros(0)
+    pct = lambda q: float(np.percentile(lat, q)) if len(lat) else None
+    cells = sum(d["cells_done"] for d in reports)
+    by = {}
+    for i, t in enumerate(tabs):
+        li = np.array([d["t_done"] - d["t_submit"] for d in done if d["mechanism"] == i])
+        by[t.name] = {"sm_share": share[i], "offered_requests": sum(1 for r in reqs if r[1] == i),
+                      "offered_cells": int(sum(r[2] for r in reqs if r[1] == i)),
+                      "completed_requests": int(len(li)),
+                      "cells_solved": int(sum(d["cells_done"] for d in reports
+                                              if d["mechanism"] == i)),
+                      "latency_p50_s": float(np.percentile(li, 50)) if len(li) else None,
+                      "latency_p99_s": float(np.percentile(li, 99)) if len(li) else None,
+                      "cost_us_per_cell_full_gpu": cost[i] * 1e6}
+    # bytes copied: every admitted request's inputs, finished requests' results
+    admitted = [d for d in reports if d["t_admit"] > 0]
+    h2d = sum(d["n_cells"] * (8 * (2 + tabs[d["mechanism"]].n_species)) for d in admitted)
+    d2h = sum(d["n_cells"] * (8 * (1 + tabs[d["mechanism"]].n_species) + 5) for d in done)
+    return {"arm": arm, "value": cells / elapsed, "unit": UNIT, "elapsed_s": elapsed,
+            "rate_req_per_s": rate, "arrival_window_s": seconds,
+            "offered_requests": len(reqs), "offered_cells": int(sum(r[2] for r in reqs)),
+            "offered_cells_per_s": sum(r[2] for r in reqs) / seconds,
+            "completed_requests": len(done),
+            "completed_cells": int(sum(d["n_cells"] for d in done)), "cells_solved": int(cells),
+            "latency_p50_s": pct(50), "latency_p99_s": pct(99),
+            "latency_max_s": float(lat.max()) if len(lat) else None,
+            "backlog_requests": int(len(reqs) - len(done)),
+            "submit_lag_max_s": lag, "peak_resident_gb": st["peak_resident_bytes"] / 2**30,
+            "kernel_launches": int(st["kernel_launches"]),
+            "h2d_bytes": int(h2d), "d2h_bytes": int(d2h),
+            "by_mechanism": by, "clocks": clk.summary(), "server_clock_start": c0}
+
+
+def run_serve(args):
+    """Serving workload: mixed+MLP and plain FP64 under the same request stream."""
+    import torch
+    torch.cuda.set_device(0)
+    arms = [serve_arm("mixed+mlp", args)]
+    if not args.no_fp64_compare:
+        arms.append(serve_arm("fp64", args))
+    a = arms[0]
+    # the same stream at a load the mixed+MLP server sustains: half of the cell
+    # rate it reached above, as requests per second of the mean request size
+    light = None
+    if args.serve_light_seconds > 0:
+        mean_cells = a["offered_cells"] / max(a["offered_requests"], 1)
+        lam = 0.5 * a["value"] / mean_cells
+        light = {"rate_req_per_s": lam, "arms": [
+            serve_arm(arm, args, rate=lam, seconds=args.serve_light_seconds,
+                      drain=args.serve_light_seconds)
+            for arm in (["mixed+mlp"] + ([] if args.no_fp64_compare else ["fp64"]))]}
+    line = {"metric": "cell-solves/s under serving load (Poisson %g req/s, %g s, sizes "
+                      "log-uniform 1k-512k, 8/20 and 32/150 mechanisms, 40 GB budget); "
+                      "p50/p99 latency" % (args.serve_rate, args.serve_seconds),
+            "value": a["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": a["elapsed_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serving: Poisson %g req/s for %g s (+%g s drain), sizes "
+                                   "log-uniform 1k-512k cells, syn8x20 and syn32x150 half and "
+                                   "half, dt 1e-3 s, 40 GB admission budget"
+                                   % (args.serve_rate, args.serve_seconds, args.serve_drain),
+                       "l2": "request inputs stream from host memory; pools of 512k cells "
+                             "per mechanism (> L2)"},
+            "latency_p50_s": a["latency_p50_s"], "latency_p99_s": a["latency_p99_s"],
+            "e2e": {"value": a["value"], "unit": UNIT, "h2d_bytes_per_step": a["h2d_bytes"],
+                    "d2h_bytes_per_step": a["d2h_bytes"],
+                    "note": "the serving value is host to host: every request's copies are in it"},
+            "gpu_launches": a["kernel_launches"], "serving": arms[0],
+            "plain_fp64": arms[1] if len(arms) > 1 else None, "light_load": light,
+            "clocks": a["clocks"]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_1905_09395_b300 import Mechanism, binding
@@ -361,6 +532,7 @@ def run_ours(args):
         e2e = {"value": n * world * ke / el, "unit": UNIT,
                "h2d_bytes_per_step": int(hT.nbytes + hP.nbytes + hY.nbytes),
                "d2h_bytes_per_step": int(sum(x.nbytes for x in ho)), "steps": ke}
+    trained_scale = m.mlp_params() if args.thermo == "mlp" else None
     m.close()
 
     def one_solve(mc, ops):
@@ -437,6 +609,18 @@ def run_ours(args):
             "mixed_poly": mixed_poly, "plain_fp64": plain, "thermo_net": mlp_info,
             "wall_s_timed": wall}
     line["clocks"] = clk.summary()
+    if world == 1 and not args.no_serve and args.precision == "mixed" and args.thermo == "mlp":
+        # p50/p99 latency under the serving load (the scale mechanism's network reused)
+        sv = serve_arm("mixed+mlp", args, trained=[None, trained_scale])
+        line["serving"] = {k: sv[k] for k in (
+            "value", "unit", "rate_req_per_s", "arrival_window_s", "elapsed_s",
+            "offered_cells_per_s", "completed_requests", "offered_requests", "cells_solved",
+            "latency_p50_s", "latency_p99_s", "latency_max_s", "by_mechanism", "clocks")}
+        line["serving"]["workload"] = ("Poisson %g req/s for %g s (+%g s), sizes log-uniform "
+                                       "1k-512k, syn8x20 and syn32x150 half and half, 40 GB "
+                                       "budget, host to host" % (args.serve_rate,
+                                                                 args.serve_seconds,
+                                                                 args.serve_drain))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **extra)
     print(json.dumps(line))
@@ -449,8 +633,18 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["scale", "uneven"], default="scale",
-                    help="uneven: 64 uneven 53/325 batches in one batched launch")
+    ap.add_argument("--workload", choices=["scale", "uneven", "serve"], default="scale",
+                    help="uneven: 64 uneven 53/325 batches in one batched launch; serve: "
+                         "the request loop, mixed+MLP and plain FP64")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window")
+    ap.add_argument("--serve-drain", type=float, default=5.0,
+                    help="seconds after the last arrival before unfinished requests are cancelled")
+    ap.add_argument("--serve-light-seconds", type=float, default=60.0,
+                    help="serve workload: arrival window of the run at half the measured "
+                         "mixed+MLP capacity (0 skips it)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="scale workload: skip the serving run beside the headline")
     ap.add_argument("--uneven-scale", type=float, default=1.0,
                     help="multiplies every batch size of the uneven workload")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
@@ -473,6 +667,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -189,11 +189,14 @@ long stev_mlp_num_params(const stev_mechanism *mech);
 
 /* Trains the network on the GPU with the library's own kernels: targets are
  * the NASA-7 polynomials at the given HOST temperatures (FP64, stored FP32,
- * standardised per output), FP32 forward/backward, Adam (lr, beta 0.9/0.999)
- * over minibatches of `batch` samples for `epochs` epochs, weights
- * initialised Xavier-uniform from splitmix64(seed).  loss_per_epoch (host,
- * nullable) receives each epoch's mean squared error in standardised units.
- * Afterwards inference uses BF16 copies of W2, W3.  Synchronous. */
+ * standardised per output), FP32 forward/backward, Adam (beta 0.9/0.999)
+ * over minibatches of `batch` samples in sample order for `epochs` epochs,
+ * the step size decaying from lr to lr/100 along a cosine, weights
+ * initialised Xavier-uniform from splitmix64(seed).  Gradients are summed
+ * over 64-sample tiles in a fixed order, so the same inputs train the same
+ * network bit for bit.  loss_per_epoch (host, nullable) receives each epoch's
+ * mean squared error in standardised units.  Afterwards inference uses BF16
+ * copies of W2, W3.  Synchronous. */
 stev_status stev_mlp_train(stev_mechanism *mech, const double *T_samples, long n_samples,
                            int epochs, int batch, float lr, unsigned long long seed,
                            float *loss_per_epoch);
@@ -216,6 +219,93 @@ stev_status stev_mlp_loss_grad(stev_mechanism *mech, const float *params, const 
  * S/R) in the order above.  Asynchronous on cuda_stream. */
 stev_status stev_mlp_eval(stev_mechanism *mech, const double *T, long n, float *props,
                           void *cuda_stream);
+
+/* ---- serving: continuous batching of solve requests.
+ * Requests (independent cell batches, each with its own t_f, from concurrent
+ * CFD steps) arrive over time.  A server keeps one persistent kernel per
+ * mechanism resident on its own share of the SMs and feeds it requests as
+ * they are admitted: a cell slot freed by a finished cell takes the next
+ * cell of the oldest unfinished request (the variable loading of Sec. 2.4,
+ * across requests).  Each cell's result is the one stev_solve gives it.
+ *
+ * Admission is first-come first-served by device memory: a request needs
+ *   2*align(8n) + align(8nS) + align(4n) + align(n)   bytes (align = 256)
+ * of the server's arena (allocated once, at creation, to mem_budget bytes;
+ * nothing is allocated while serving), and one of queue_len slots of its
+ * mechanism.  A worker thread in the library makes every CUDA call of the
+ * server: input copies, launches, completion polling (a host-mapped mailbox
+ * written by each request's last cell) and result copies, on streams of its
+ * own.  While a server holds a mechanism, do not change the mechanism's
+ * options or network, and do not destroy it. */
+typedef struct stev_server stev_server; /* opaque */
+
+typedef struct {
+  long long id;    /* from stev_server_submit */
+  int mechanism;   /* index into the server's mechanism list */
+  int status;      /* STEV_OK: results are in the host arrays;
+                      STEV_EINCOMPLETE: cancelled by stev_server_destroy */
+  long n_cells;
+  long cells_done; /* cells solved: n_cells when finished; for a cancelled
+                      request, those whose results were written on the device
+                      before the kernels stopped (not copied back) */
+  double t_submit; /* seconds on the server clock (stev_server_clock): submitted, */
+  double t_admit;  /*   admitted (arena range reserved, copies queued), */
+  double t_done;   /*   results copied to the host arrays */
+} stev_request_info;
+
+typedef struct {
+  long long submitted, admitted, completed, cancelled;
+  long long cells_completed;
+  size_t resident_bytes;       /* arena bytes held by admitted, unfinished requests */
+  size_t peak_resident_bytes;
+  size_t budget_bytes;
+  long long kernel_launches;   /* persistent-kernel (re)launches */
+} stev_server_stats;
+
+/* Creates a server for n_mechs mechanisms (all on the current device).
+ * sm_share[i] (HOST, nullable = even split) is the number of SMs whose single
+ * CTA runs mechanism i's kernel; the shares may add up to at most the SM
+ * count.  mem_budget: bytes of the device arena.  queue_len: request slots per
+ * mechanism (0 = 1024).  Errors: STEV_EINVAL (bad arguments, a mechanism with
+ * thermo = MLP and no trained network), STEV_ENOMEM (the arena), STEV_ECUDA. */
+stev_status stev_server_create(stev_mechanism *const *mechs, int n_mechs, const int *sm_share,
+                               size_t mem_budget, int queue_len, stev_server **out);
+
+/* Queues a request of n_cells cells of mechanism `mech` (HOST arrays, layouts
+ * as for stev_solve; pinned memory makes the copies asynchronous).  The arrays
+ * must stay valid and untouched until the request is reported by
+ * stev_server_poll.  Returns at once; *request_id (nullable) gets the id.
+ * Errors: STEV_EINVAL for bad arguments or a request larger than the whole
+ * budget; the error of a failed server. */
+stev_status stev_server_submit(stev_server *srv, int mech, long n_cells, double dt_cfd,
+                               const double *T, const double *P, const double *Y,
+                               double *T_out, double *Y_out, int *iters,
+                               unsigned char *cell_status, long long *request_id);
+
+/* Moves up to max_done finished requests into done[] (HOST), oldest first,
+ * waiting up to timeout_s seconds for the first one if none is ready.
+ * *n_done gets the count.  Returns the server's error if its worker failed. */
+stev_status stev_server_poll(stev_server *srv, stev_request_info *done, int max_done,
+                             int *n_done, double timeout_s);
+
+/* Copies the server's counters into *stats. */
+stev_status stev_server_get_stats(stev_server *srv, stev_server_stats *stats);
+
+/* Seconds since the server was created (the clock of stev_request_info). */
+double stev_server_clock(const stev_server *srv);
+
+/* Stops the server: no more submissions; kernels finish the cells they hold,
+ * claim no more and leave.  Requests whose cells all finished get their
+ * results; the rest are reported STEV_EINCOMPLETE with their cells_done.
+ * Every report stays readable with stev_server_poll until destroy.  Waits at
+ * most timeout_s (<= 0: 30 s) for the kernels to leave; STEV_ETIMEOUT if they
+ * did not.  Calling it again returns the first call's outcome. */
+stev_status stev_server_stop(stev_server *srv, double timeout_s);
+
+/* Stops the server if needed (as stev_server_stop) and frees it; unread
+ * reports are lost.  If the kernels did not leave in time (STEV_ETIMEOUT) the
+ * device buffers are not freed.  NULL is a no-op. */
+stev_status stev_server_destroy(stev_server *srv, double timeout_s);
 
 /* Number of resident solver slots (cells in flight) of the persistent kernel
  * on the current device for this mechanism and its options. */

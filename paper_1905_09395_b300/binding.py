@@ -29,6 +29,8 @@ EXPORTS = (
     "stev_resident_slots", "stev_destroy", "stev_last_error", "stev_solve_host_noalloc",
     "stev_mlp_num_params", "stev_mlp_train", "stev_mlp_set_params", "stev_mlp_get_params",
     "stev_mlp_loss_grad", "stev_mlp_eval", "stev_solve_batched",
+    "stev_server_create", "stev_server_submit", "stev_server_poll", "stev_server_get_stats",
+    "stev_server_clock", "stev_server_stop", "stev_server_destroy",
 )
 
 
@@ -47,6 +49,24 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("thermo", ctypes.c_int), ("dft_on", ctypes.c_int),
         ("lanes_per_cell", ctypes.c_int),
     ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("mechanism", ctypes.c_int), ("status", ctypes.c_int),
+                ("n_cells", ctypes.c_long), ("cells_done", ctypes.c_long),
+                ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("cancelled", ctypes.c_longlong),
+                ("cells_completed", ctypes.c_longlong), ("resident_bytes", ctypes.c_size_t),
+                ("peak_resident_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +110,20 @@ def lib():
         L.stev_mlp_eval.restype = I
         L.stev_solve_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P]
         L.stev_solve_batched.restype = I
+        L.stev_server_create.argtypes = [P, I, P, ctypes.c_size_t, I, P]
+        L.stev_server_create.restype = I
+        L.stev_server_submit.argtypes = [P, I, LNG, D, P, P, P, P, P, P, P, P]
+        L.stev_server_submit.restype = I
+        L.stev_server_poll.argtypes = [P, P, I, P, D]
+        L.stev_server_poll.restype = I
+        L.stev_server_get_stats.argtypes = [P, P]
+        L.stev_server_get_stats.restype = I
+        L.stev_server_clock.argtypes = [P]
+        L.stev_server_clock.restype = D
+        L.stev_server_stop.argtypes = [P, D]
+        L.stev_server_stop.restype = I
+        L.stev_server_destroy.argtypes = [P, D]
+        L.stev_server_destroy.restype = I
         L.stev_resident_slots.argtypes = [P]
         L.stev_resident_slots.restype = LNG
         L.stev_destroy.argtypes = [P]
@@ -289,6 +323,99 @@ class Mechanism:
         if self._h:
             lib().stev_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a):
+    """Address of a contiguous host array (numpy array or CPU torch tensor)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host arrays must be contiguous")
+        return a.ctypes.data
+    if getattr(a, "is_cuda", False) or not a.is_contiguous():
+        raise ValueError("host arrays must be contiguous CPU tensors")
+    return a.data_ptr()
+
+
+class Server:
+    """Continuous-batching solve server (stev_server_*).
+
+    mechanisms: Mechanism objects (kept alive by the server); sm_share: SMs per
+    mechanism (None = even split); mem_budget: bytes of the device arena;
+    queue_len: request slots per mechanism (0 = library default)."""
+
+    def __init__(self, mechanisms, sm_share=None, mem_budget: int = 1 << 30,
+                 queue_len: int = 0):
+        self.mechanisms = list(mechanisms)
+        self._h = ctypes.c_void_p()
+        hs = (ctypes.c_void_p * len(self.mechanisms))(*[m._h.value for m in self.mechanisms])
+        share = None
+        if sm_share is not None:
+            share = (ctypes.c_int * len(self.mechanisms))(*[int(x) for x in sm_share])
+        _check(lib().stev_server_create(hs, len(self.mechanisms), share, int(mem_budget),
+                                        int(queue_len), ctypes.byref(self._h)))
+        self._live = {}
+
+    def submit(self, mech: int, T, P, Y, dt: float, out=None) -> int:
+        """Queues a request (host arrays; pinned memory copies asynchronously).
+        out = (T_out, Y_out, iters, status) host arrays, allocated if None.
+        The arrays are held until poll() reports the request."""
+        S = self.mechanisms[mech].S
+        n = int(T.shape[0])
+        if tuple(P.shape) != (n,) or tuple(Y.shape) != (n, S):
+            raise ValueError("bad shapes")
+        if out is None:
+            out = (np.empty(n), np.empty((n, S)), np.empty(n, np.int32), np.empty(n, np.uint8))
+        rid = ctypes.c_longlong(-1)
+        ptrs = [_host_ptr(a) for a in (T, P, Y) + tuple(out)]
+        _check(lib().stev_server_submit(self._h, int(mech), n, float(dt), *ptrs,
+                                        ctypes.byref(rid)))
+        self._live[rid.value] = ((T, P, Y), out)
+        return rid.value
+
+    def poll(self, timeout: float = 0.0, max_done: int = 1024):
+        """Finished requests: a list of dicts (id, mechanism, status, n_cells,
+        t_submit, t_admit, t_done, out=(T_out, Y_out, iters, status))."""
+        buf = (RequestInfo * max_done)()
+        k = ctypes.c_int(0)
+        _check(lib().stev_server_poll(self._h, buf, max_done, ctypes.byref(k), float(timeout)))
+        res = []
+        for i in range(k.value):
+            r = buf[i]
+            d = {f: getattr(r, f) for f, _ in RequestInfo._fields_}
+            d["out"] = self._live.pop(r.id, (None, None))[1]
+            res.append(d)
+        return res
+
+    @property
+    def stats(self):
+        st = ServerStats()
+        _check(lib().stev_server_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def clock(self) -> float:
+        return float(lib().stev_server_clock(self._h))
+
+    def stop(self, timeout: float = 30.0):
+        """Stops serving (stev_server_stop); poll() still returns every report,
+        cancelled requests with status STEV_EINCOMPLETE and their cells_done."""
+        _check(lib().stev_server_stop(self._h, float(timeout)))
+
+    def close(self, timeout: float = 30.0):
+        """Stops the server (stev_server_destroy); poll() first for reports."""
+        if not self._h:
+            return
+        code = lib().stev_server_destroy(self._h, float(timeout))
+        msg = lib().stev_last_error().decode()
+        self._h = ctypes.c_void_p()
+        self._live.clear()
+        if code != STEV_OK:
+            raise StevError(code, msg)
 
     def __del__(self):
         try:

@@ -14,6 +14,7 @@
 
 #include "../../include/stev.h"
 #include "stev_device.cuh"
+#include "stev_internal.h"
 #include "stev_fp64.cuh"
 #include "stev_mixed.cuh"
 #include "stev_mlp.cuh"
@@ -23,7 +24,9 @@ using namespace stev;
 // ----------------------------------------------------------------- errors
 static thread_local std::string g_err;
 
-static stev_status fail(stev_status st, const char* fmt, ...) {
+namespace stev {
+namespace host {
+stev_status fail(stev_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -32,6 +35,10 @@ static stev_status fail(stev_status st, const char* fmt, ...) {
   g_err = buf;
   return st;
 }
+void clear_error() { g_err.clear(); }
+}  // namespace host
+}  // namespace stev
+using stev::host::fail;
 
 #define CUDA_TRY(expr)                                                                   \
   do {                                                                                   \
@@ -59,6 +66,7 @@ struct stev_mechanism {
   // launch configuration of the persistent kernel
   int G = 32;              // lanes per cell
   int block = 0, grid = 0; // threads per CTA, CTAs
+  int per_sm = 0, sms = 0;  // resident CTAs per SM, SMs
   size_t smem = 0;
   long long nslots = 0;    // cells resident at once
   unsigned long long* d_counter = nullptr;
@@ -135,11 +143,11 @@ typedef void (*KernelFn)(Launch);
 
 static KernelFn select_kernel(int precision, int G, int thermo = STEV_THERMO_POLY) {
   if (precision == STEV_MIXED) {
-    if (thermo != STEV_THERMO_POLY) return stev_mixed_kernel<32, true>;
+    if (thermo != STEV_THERMO_POLY) return stev_mixed_net_kernel;
     switch (G) {
-      case 8: return stev_mixed_kernel<8, false>;
-      case 16: return stev_mixed_kernel<16, false>;
-      default: return stev_mixed_kernel<32, false>;
+      case 8: return stev_mixed_kernel<8>;
+      case 16: return stev_mixed_kernel<16>;
+      default: return stev_mixed_kernel<32>;
     }
   }
   switch (G) {
@@ -177,19 +185,23 @@ static stev_status configure(stev_mechanism* m) {
   const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n, net)
                             : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
   const size_t limit = prop.sharedMemPerBlockOptin;
-  if (tables + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
-  int cells = (int)((limit - tables) / cell);
+  // the network kernel adds per-CTA buffers (sized here for its largest CTA)
+  const size_t extra = net ? net_cta_smem_bytes(kMaxBlockMixedNet / 32) : 0;
+  if (tables + extra + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
+  int cells = (int)((limit - tables - extra) / cell);
   cells = std::min(cells, (mixed ? (net ? kMaxBlockMixedNet : kMaxBlockMixed) : kMaxBlock) / G);
   const int per_warp = 32 / G;
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
-  const size_t smem = tables + (size_t)cells * cell;
+  const size_t smem = tables + (size_t)cells * cell + (net ? net_cta_smem_bytes(cells) : 0);
   KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo);
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cells * G, smem));
   if (per_sm < 1) return fail(STEV_EINVAL, "persistent kernel cannot be resident");
   m->block = cells * G;
+  m->per_sm = per_sm;
+  m->sms = prop.multiProcessorCount;
   m->grid = per_sm * prop.multiProcessorCount;
   m->smem = smem;
   m->nslots = (long long)m->grid * cells;
@@ -578,6 +590,43 @@ extern "C" stev_status stev_solve_host(stev_mechanism* m, long n, const double* 
   return STEV_OK;
 }
 
+// ------------------------------------------------------ serving interface
+namespace stev {
+namespace host {
+
+stev_status serve_config(const stev_mechanism* m, ServeConfig* out) {
+  if (!m) return fail(STEV_EINVAL, "mechanism is NULL");
+  if (m->opt.thermo != STEV_THERMO_POLY && !m->mlp_ready)
+    return fail(STEV_EINVAL, "thermo = MLP needs a trained network (stev_mlp_train or stev_mlp_set_params)");
+  out->device = m->device;
+  out->S = m->S;
+  out->ctas_per_sm = m->per_sm;
+  out->sms = m->sms;
+  out->cells_per_cta = m->block / m->G;
+  return STEV_OK;
+}
+
+stev_status serve_launch(stev_mechanism* m, ServeCtl* ctl, ServeSlot* slots,
+                         volatile long long* mail, int q, long long idle_ns, int grid,
+                         cudaStream_t s) {
+  Launch L = make_launch(m, 0, 1.0);
+  L.serve = 1;
+  L.ctl = ctl;
+  L.slots = slots;
+  L.smail = mail;
+  L.serve_q = q;
+  L.idle_ns = idle_ns;
+  L.serve_warps = grid * (m->block / 32);
+  L.y_soa = 0;
+  CUDA_TRY(cudaMemsetAsync(&ctl->idle_warps, 0, 2 * sizeof(int), s));  // idle_warps, exiting
+  select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<grid, m->block, m->smem, s>>>(L);
+  CUDA_TRY(cudaGetLastError());
+  return STEV_OK;
+}
+
+}  // namespace host
+}  // namespace stev
+
 extern "C" void stev_destroy(stev_mechanism* m) {
   if (!m) return;
   cudaDeviceSynchronize();
@@ -777,16 +826,17 @@ extern "C" stev_status stev_mlp_get_params(const stev_mechanism* m, float* param
   return STEV_OK;
 }
 
-// Gradient of the mean-squared error of the network with parameters
-// `params` on n samples (standardised targets), through the training kernel.
+// Per-tile gradients and squared errors of the network with parameters
+// `params` on n samples (standardised targets), through the training kernel:
+// part [tiles][n_params], loss_part [tiles], tiles = ceil(n / kMlpTile).
 static stev_status mlp_grad_device(stev_mechanism* m, const float* d_params, const double* d_T,
                                    const float* d_target, long long n, long long n_total,
-                                   float* d_grad, double* d_loss, cudaStream_t s) {
+                                   float* d_part, double* d_loss_part, cudaStream_t s) {
   const size_t smem = mlp_grad_smem_bytes(m->mlp_out);
   CUDA_TRY(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int blocks = (int)((n + kMlpTile - 1) / kMlpTile);
   mlp_grad_kernel<<<blocks, kMlpTile, smem, s>>>(d_params, m->mlp_out, d_T, d_target, n, n_total,
-                                                 d_grad, d_loss);
+                                                 d_part, d_loss_part);
   CUDA_TRY(cudaGetLastError());
   return STEV_OK;
 }
@@ -799,10 +849,14 @@ extern "C" stev_status stev_mlp_loss_grad(stev_mechanism* m, const float* params
   if (n < 1) return fail(STEV_EINVAL, "n < 1");
   const int np = mlp_n_params(3 * m->S), no = 3 * m->S;
   m->mlp_out = no;
-  float *dp = nullptr, *dt = nullptr, *dg = nullptr;
-  double *dT = nullptr, *dl = nullptr;
+  const int tiles = (int)((n + kMlpTile - 1) / kMlpTile);
+  float *dp = nullptr, *dt = nullptr, *dg = nullptr, *dpart = nullptr;
+  double *dT = nullptr, *dl = nullptr, *dlp = nullptr;
   stev_status st = STEV_OK;
-  auto cleanup = [&]() { cudaFree(dp); cudaFree(dt); cudaFree(dg); cudaFree(dT); cudaFree(dl); };
+  auto cleanup = [&]() {
+    cudaFree(dp); cudaFree(dt); cudaFree(dg); cudaFree(dT); cudaFree(dl); cudaFree(dpart);
+    cudaFree(dlp);
+  };
 #define TRY_CLEAN(expr)                                                                     \
   do {                                                                                      \
     cudaError_t e_ = (expr);                                                                \
@@ -816,13 +870,16 @@ extern "C" stev_status stev_mlp_loss_grad(stev_mechanism* m, const float* params
   TRY_CLEAN(cudaMalloc(&dt, (size_t)n * no * 4));
   TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
   TRY_CLEAN(cudaMalloc(&dl, 8));
+  TRY_CLEAN(cudaMalloc(&dpart, (size_t)tiles * np * 4));
+  TRY_CLEAN(cudaMalloc(&dlp, (size_t)tiles * 8));
   TRY_CLEAN(cudaMemcpy(dp, params, (size_t)np * 4, cudaMemcpyHostToDevice));
   TRY_CLEAN(cudaMemcpy(dt, target, (size_t)n * no * 4, cudaMemcpyHostToDevice));
   TRY_CLEAN(cudaMemcpy(dT, T, (size_t)n * 8, cudaMemcpyHostToDevice));
-  TRY_CLEAN(cudaMemset(dg, 0, (size_t)np * 4));
   TRY_CLEAN(cudaMemset(dl, 0, 8));
-  st = mlp_grad_device(m, dp, dT, dt, n, n, dg, dl, 0);
+  st = mlp_grad_device(m, dp, dT, dt, n, n, dpart, dlp, 0);
   if (st == STEV_OK) {
+    mlp_sum_kernel<<<(np + 255) / 256, 256>>>(dpart, tiles, np, dlp, dg, dl);
+    TRY_CLEAN(cudaGetLastError());
     TRY_CLEAN(cudaMemcpy(grad, dg, (size_t)np * 4, cudaMemcpyDeviceToHost));
     TRY_CLEAN(cudaMemcpy(loss, dl, 8, cudaMemcpyDeviceToHost));
     *loss /= (double)n * no;
@@ -850,11 +907,13 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   stev_status st = mlp_ensure(m);
   if (st != STEV_OK) return st;
   const int no = m->mlp_out, np = m->mlp_np;
-  double *dT = nullptr, *dsum = nullptr, *dloss = nullptr;
-  float *dtarget = nullptr, *dgrad = nullptr, *dm1 = nullptr, *dm2 = nullptr, *dstat = nullptr;
+  const int mb_tiles = (int)((std::min((long long)batch, (long long)n) + kMlpTile - 1) / kMlpTile);
+  const int mom_blocks = 64;
+  double *dT = nullptr, *dsum = nullptr, *dloss = nullptr, *dlp = nullptr;
+  float *dtarget = nullptr, *dpart = nullptr, *dm1 = nullptr, *dm2 = nullptr, *dstat = nullptr;
   auto cleanup = [&]() {
-    cudaFree(dT); cudaFree(dsum); cudaFree(dloss); cudaFree(dtarget); cudaFree(dgrad);
-    cudaFree(dm1); cudaFree(dm2); cudaFree(dstat);
+    cudaFree(dT); cudaFree(dsum); cudaFree(dloss); cudaFree(dtarget); cudaFree(dpart);
+    cudaFree(dm1); cudaFree(dm2); cudaFree(dstat); cudaFree(dlp);
   };
 #define TRY_CLEAN(expr)                                                                     \
   do {                                                                                      \
@@ -867,9 +926,10 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   } while (0)
   TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
   TRY_CLEAN(cudaMalloc(&dtarget, (size_t)n * no * 4));
-  TRY_CLEAN(cudaMalloc(&dsum, (size_t)2 * no * 8));
+  TRY_CLEAN(cudaMalloc(&dsum, (size_t)2 * no * mom_blocks * 8));
   TRY_CLEAN(cudaMalloc(&dstat, (size_t)2 * no * 4));
-  TRY_CLEAN(cudaMalloc(&dgrad, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dpart, (size_t)mb_tiles * np * 4));
+  TRY_CLEAN(cudaMalloc(&dlp, (size_t)mb_tiles * 8));
   TRY_CLEAN(cudaMalloc(&dm1, (size_t)np * 4));
   TRY_CLEAN(cudaMalloc(&dm2, (size_t)np * 4));
   TRY_CLEAN(cudaMalloc(&dloss, 8));
@@ -879,16 +939,20 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
     const long long tot = (long long)n * m->S;
     mlp_targets_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(m->d_sp, m->S, dT, n, dtarget);
     TRY_CLEAN(cudaGetLastError());
-    TRY_CLEAN(cudaMemset(dsum, 0, (size_t)2 * no * 8));
-    mlp_moments_kernel<<<dim3(64, no), 256>>>(dtarget, n, no, dsum, dsum + no);
+    mlp_moments_kernel<<<dim3(mom_blocks, no), 256>>>(dtarget, n, no, dsum);
     TRY_CLEAN(cudaGetLastError());
   }
-  std::vector<double> sums((size_t)2 * no);
-  TRY_CLEAN(cudaMemcpy(sums.data(), dsum, sums.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> parts((size_t)2 * no * mom_blocks);
+  TRY_CLEAN(cudaMemcpy(parts.data(), dsum, parts.size() * 8, cudaMemcpyDeviceToHost));
   std::vector<float> mean(no), stdv(no), inv(no);
   for (int c = 0; c < no; ++c) {
-    const double mu = sums[c] / n;
-    const double var = std::max(sums[no + c] / n - mu * mu, 0.0);
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < mom_blocks; ++b) {
+      s1 += parts[((size_t)c * mom_blocks + b) * 2];
+      s2 += parts[((size_t)c * mom_blocks + b) * 2 + 1];
+    }
+    const double mu = s1 / n;
+    const double var = std::max(s2 / n - mu * mu, 0.0);
     mean[c] = (float)mu;
     stdv[c] = (float)std::max(std::sqrt(var), 1e-6 * std::max(1.0, std::fabs(mu)));
     inv[c] = 1.0f / stdv[c];
@@ -909,22 +973,27 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   for (int k = 0; k < kHid * kHid; ++k) P[o.W2 + k] = uni(std::sqrt(6.0f / (kHid + kHid)));
   for (int k = 0; k < no * kHid; ++k) P[o.W3 + k] = uni(std::sqrt(6.0f / (kHid + no)));
   TRY_CLEAN(cudaMemcpy(m->d_mlp_params, P.data(), (size_t)np * 4, cudaMemcpyHostToDevice));
-  TRY_CLEAN(cudaMemset(dgrad, 0, (size_t)np * 4));
   TRY_CLEAN(cudaMemset(dm1, 0, (size_t)np * 4));
   TRY_CLEAN(cudaMemset(dm2, 0, (size_t)np * 4));
-  // Adam over minibatches in sample order (the samples are drawn independently)
+  // Adam over minibatches in sample order (the samples are drawn
+  // independently), the step size decaying from lr to lr/100 along a cosine
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const long long per_epoch = (n + batch - 1) / batch, total = per_epoch * epochs;
   long long step = 0;
   for (int ep = 0; ep < epochs; ++ep) {
     TRY_CLEAN(cudaMemset(dloss, 0, 8));
     for (long long s0 = 0; s0 < n; s0 += batch) {
       const long long nb = std::min((long long)batch, (long long)n - s0);
-      st = mlp_grad_device(m, m->d_mlp_params, dT + s0, dtarget + s0 * no, nb, nb, dgrad, dloss, 0);
+      const int tiles = (int)((nb + kMlpTile - 1) / kMlpTile);
+      st = mlp_grad_device(m, m->d_mlp_params, dT + s0, dtarget + s0 * no, nb, nb, dpart, dlp, 0);
       if (st != STEV_OK) { cleanup(); return st; }
+      const double frac = (double)step / (double)std::max(total - 1, 1LL);
+      const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac))));
       ++step;
-      // the loss accumulated by each minibatch is its own mean; average below
+      // each minibatch's squared errors are relative to its own mean; averaged below
       const float bc1 = 1.0f - std::pow(b1, (float)step), bc2 = 1.0f - std::pow(b2, (float)step);
-      mlp_adam_kernel<<<(np + 255) / 256, 256>>>(m->d_mlp_params, dgrad, dm1, dm2, np, lr, b1, b2, eps, bc1, bc2);
+      mlp_adam_kernel<<<(np + 255) / 256, 256>>>(m->d_mlp_params, dpart, tiles, dlp, dloss, dm1,
+                                                 dm2, np, lr_t, b1, b2, eps, bc1, bc2);
       TRY_CLEAN(cudaGetLastError());
     }
     if (loss_per_epoch) {

@@ -62,7 +62,19 @@ struct CellIO {
 
 __device__ __forceinline__ CellIO cell_io(const Launch& L, int b) {
   CellIO io;
-  if (L.nb > 0) {
+  if (L.serve) {
+    // slots are rewritten by the host between requests: read around L1
+    const BatchDesc* d = &L.slots[b].d;
+    io.T = (const double*)__ldcg((const long long*)&d->T);
+    io.P = (const double*)__ldcg((const long long*)&d->P);
+    io.Y = (const double*)__ldcg((const long long*)&d->Y);
+    io.T_out = (double*)__ldcg((const long long*)&d->T_out);
+    io.Y_out = (double*)__ldcg((const long long*)&d->Y_out);
+    io.iters = (int*)__ldcg((const long long*)&d->iters);
+    io.status = (unsigned char*)__ldcg((const long long*)&d->status);
+    io.dt = __ldcg(&d->dt);
+    io.n = __ldcg(&d->n);
+  } else if (L.nb > 0) {
     const BatchDesc& d = L.bdesc[b];
     io.T = d.T; io.P = d.P; io.Y = d.Y; io.T_out = d.T_out; io.Y_out = d.Y_out;
     io.iters = d.iters; io.status = d.status; io.dt = d.dt; io.n = d.n;
@@ -71,6 +83,144 @@ __device__ __forceinline__ CellIO cell_io(const Launch& L, int b) {
     io.iters = L.iters; io.status = L.status; io.dt = L.dt; io.n = L.n_cells;
   }
   return io;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long ld_acquire_s64(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Serving refill: lane 0 claims up to one id per needy group below
+// `published` with a bounded compare-and-swap loop; needy groups take them in
+// lane order.  `idle` (warp-uniform) is set when ids were wanted but none were
+// ready, so that the caller can back off.
+template <int G>
+__device__ __forceinline__ long long serve_refill(const Launch& L, bool needs, bool& idle) {
+  const int lane = threadIdx.x & 31;
+  const int leader = lane & ~(G - 1);
+  const unsigned need = __ballot_sync(0xffffffffu, (lane == leader) && needs);
+  idle = false;
+  if (need == 0u) return -1;
+  const unsigned cnt = __popc(need);
+  unsigned long long base = 0, got = 0;
+  if (lane == 0 && *(volatile int*)&L.ctl->stop == 0 && *(volatile int*)&L.ctl->exiting == 0) {
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      const unsigned long long pub = ld_acquire_u64(&L.ctl->published);
+      const unsigned long long cur = *(volatile unsigned long long*)&L.ctl->claim;
+      if (cur >= pub) break;
+      const unsigned long long want = min((unsigned long long)cnt, pub - cur);
+      if (atomicCAS(&L.ctl->claim, cur, cur + want) == cur) {
+        base = cur;
+        got = want;
+        break;
+      }
+    }
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  got = __shfl_sync(0xffffffffu, got, 0);
+  idle = got == 0;
+  if (!needs) return -1;
+  const unsigned rank = __popc(need & ((1u << leader) - 1u));
+  return rank < got ? (long long)(base + rank) : -1;
+}
+
+// Serving: a warp with no cell.  Returns true when the warp should leave:
+// on `stop`, once `exiting` is set, or when it finds every warp of the grid
+// idle for idle_ns (it then sets `exiting`).  `committed` (warp-uniform) tells
+// whether this warp counts itself in idle_warps; it counts itself out as soon
+// as unclaimed work is visible, before it claims any.
+__device__ __forceinline__ bool serve_idle(const Launch& L, unsigned long long& idle_since,
+                                           bool& committed) {
+  const int lane = threadIdx.x & 31;
+  int leave = 0, comm = committed ? 1 : 0;
+  if (lane == 0) {
+    ServeCtl* ctl = L.ctl;
+    const unsigned long long now = gtimer_ns();
+    if (idle_since == 0) idle_since = now;
+    if (*(volatile int*)&ctl->stop || *(volatile int*)&ctl->exiting) {
+      leave = 1;
+    } else if (*(volatile unsigned long long*)&ctl->claim < ld_acquire_u64(&ctl->published)) {
+      if (comm) {
+        atomicSub(&ctl->idle_warps, 1);
+        comm = 0;
+      }
+      idle_since = now;
+    } else {
+      if (!comm && now - idle_since > (unsigned long long)L.idle_ns) {
+        atomicAdd(&ctl->idle_warps, 1);
+        comm = 1;
+      }
+      if (comm) {
+        __threadfence();
+        if (atomicAdd(&ctl->idle_warps, 0) >= L.serve_warps) {
+          atomicExch(&ctl->exiting, 1);
+          leave = 1;
+        }
+      }
+    }
+  }
+  leave = __shfl_sync(0xffffffffu, leave, 0);
+  committed = __shfl_sync(0xffffffffu, comm, 0) != 0;
+  return leave != 0;
+}
+
+// Serving: the slot of claimed id c, by binary search over the newest serve_q
+// sequence numbers.  Slots are retired in sequence order and only a retired
+// slot is rewritten, so c's request (unfinished) is inside the window and its
+// slot is stable.  A slot older than c's request reads as its old key (first
+// id <= c) or as a newer request's key (other sequence number): both say
+// "c lies beyond", which is right.  Returns -1 if the index would fall outside
+// the request (never expected).
+__device__ __forceinline__ int serve_find_slot(const Launch& L, long long c, long long& lc) {
+  const long long hi0 = ld_acquire_s64(&L.ctl->pub_seq);
+  long long lo = max(0LL, hi0 - L.serve_q + 1), hi = hi0;  // answer in [lo, hi]
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) >> 1;
+    const unsigned long long key = __ldcg(&L.slots[(int)(mid % L.serve_q)].key);
+    const bool beyond = (key & kServeSeqMask) != ((unsigned long long)mid & kServeSeqMask) ||
+                        (long long)(key >> kServeSeqBits) <= c;
+    if (beyond) lo = mid; else hi = mid - 1;
+  }
+  const int s = (int)(lo % L.serve_q);
+  const unsigned long long key = __ldcg(&L.slots[s].key);
+  lc = c - (long long)(key >> kServeSeqBits);
+  const long long n = __ldcg(&L.slots[s].d.n);
+  if ((key & kServeSeqMask) != ((unsigned long long)lo & kServeSeqMask) || lc < 0 || lc >= n) {
+    atomicAdd(&L.ctl->dropped, 1);
+    L.smail[L.serve_q] = -2;  // tell the host
+    return -1;
+  }
+  return s;
+}
+
+// Serving: called by every lane of a group after it has written its share of
+// a finished cell's outputs.  One lane counts the cell; the request's last
+// cell posts the request's sequence number to the host mailbox.
+template <int G>
+__device__ __forceinline__ void serve_cell_done(const Launch& L, int b, long long n, int l) {
+  const unsigned gmask = (G == 32) ? 0xffffffffu
+                                   : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  __threadfence();  // this lane's outputs before the count
+  __syncwarp(gmask);
+  if (l == 0) {
+    ServeSlot* sl = L.slots + b;
+    const unsigned long long prev = atomicAdd(&sl->done, 1ULL);
+    if ((long long)prev + 1 == n) {
+      __threadfence_system();
+      L.smail[b] = (long long)__ldcg(&sl->key);
+    }
+  }
 }
 
 __device__ __forceinline__ int find_batch(const Launch& L, long long c) {

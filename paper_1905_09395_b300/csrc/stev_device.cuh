@@ -20,6 +20,8 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "stev_layout.h"
+
 namespace stev {
 
 constexpr int kMaxSpecies = 64;
@@ -64,19 +66,7 @@ struct MlpInfer {
   int n_valid;              // 3S: columns written to the caller's array
 };
 
-// One independent batch of cells in a batched launch (its own arrays, size
-// and fluid time step).  Layouts as for the single-batch entry points.
-struct BatchDesc {
-  const double* T;
-  const double* P;
-  const double* Y;        // [n][S]
-  double* T_out;
-  double* Y_out;          // [n][S]
-  int* iters;
-  unsigned char* status;
-  double dt;
-  long long n;
-};
+
 
 // Everything a launch needs, passed by value.
 struct Launch {
@@ -113,6 +103,17 @@ struct Launch {
   int nb;
   const long long* boff;  // [nb+1]
   const BatchDesc* bdesc; // [nb]
+  // serving (resident kernel fed by the host): ids below ctl->published are
+  // claimable; the request of an id is found among the newest serve_q slots;
+  // the last finished cell of a request writes its slot key to smail
+  // (host-mapped, one word per slot, then one error word)
+  int serve;
+  ServeCtl* ctl;
+  ServeSlot* slots;
+  volatile long long* smail;
+  int serve_q;
+  long long idle_ns;      // the kernel leaves once every warp has been idle this long
+  int serve_warps;        // warps in the grid
   MlpInfer mlp;           // thermo network (mixed kernel, thermo = MLP)
   int mlp_needed;         // network outputs the solver reads (cp/R [, H/R]), rounded up to 8
   int mlp_h;              // 1: H/RT from the network as well
@@ -145,13 +146,22 @@ __host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gat
 
 // Mixed kernel cell: Y in FP64 and G/RT log2 e as a float pair (8 bytes each
 // per species); C, H/RT, a float copy of Y (S each), rates (R), history
-// [N][Rrev] and rOF (Rrev) in FP32; with the thermo network also 64 BF16 of
-// its layer-1 output and its 2S (rounded up to 8) outputs.
+// [N][Rrev] and rOF (Rrev) in FP32; with the thermo network also the cell's
+// row of network outputs (2S rounded up to 8).
 __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n,
                                                        bool mlp = false) {
   size_t b = (size_t)16 * S + ((size_t)3 * S + R + (size_t)dft_n * Rrev + Rrev) * 4;
-  if (mlp) b += 64 * 2 + (size_t)((2 * S + 7) / 8 * 8) * 4;
+  if (mlp) b += (size_t)((2 * S + 7) / 8 * 8) * 4;
   return (b + 15) & ~(size_t)15;
+}
+
+// Per-CTA buffers of the network kernel for `cells` resident cells (one per
+// warp): the scaled temperatures (padded to whole 16-row tiles), one 16 x 72
+// BF16 activation tile per 16 cells, and three rotating counters.
+constexpr int kNetActLd = 64 + 8;
+__host__ __device__ inline size_t net_cta_smem_bytes(int cells) {
+  const int tiles = (cells + 15) / 16;
+  return (size_t)tiles * 16 * 4 + (size_t)tiles * 16 * kNetActLd * 2 + 16;
 }
 
 }  // namespace stev

@@ -229,29 +229,62 @@ __global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
   st.b = 0;
   st.it = 0;
   st.nhist = 0;
+  unsigned long long idle_since = 0;  // serving: when this warp last ran out of work
+  bool idle_committed = false;        // serving: counted in ctl->idle_warps
+  unsigned idle_sleep = 1000u;        // serving: ns between looks while idle
+  int serve_skip = 0;                 // serving: steps before the next look
   bool exhausted = false;  // warp-uniform
   while (true) {
-    const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
-    if (c >= 0) {
+    long long c = -1;
+    if (!L.serve) {
+      c = refill<G>(L.counter, n, st.cell < 0, exhausted);
+    } else if (serve_skip > 0) {
+      --serve_skip;  // nothing was ready recently: look again in a few steps
+    } else if (idle_committed) {
+      // counted idle: the idle path counts the warp out before it claims
+    } else {
+      bool none_ready;
+      c = serve_refill<G>(L, st.cell < 0, none_ready);
+      if (none_ready) serve_skip = 32;
+    }
+    if (c >= 0 && L.serve) {
+      st.b = serve_find_slot(L, c, st.lc);
+      if (st.b < 0) {  // dropped: counted in ctl->dropped
+        st.b = 0;
+        c = -1;
+      }
+    } else if (c >= 0) {
       st.b = find_batch(L, c);
-      const CellIO io = cell_io(L, st.b);
       st.lc = L.nb > 0 ? c - L.boff[st.b] : c;
+    }
+    if (c >= 0) {
+      const CellIO io = cell_io(L, st.b);
       const long long lc = st.lc;
       st.cell = c;
-      st.T = io.T[lc];
-      st.P = io.P[lc];
+      st.T = __ldcg(io.T + lc);  // L1 bypass: serving reuses these addresses
+      st.P = __ldcg(io.P + lc);
       st.dt = io.dt;
       st.t_rem = io.dt;
       st.it = 0;
       st.nhist = 0;
       if (L.y_soa)
-        for (int i = l; i < S; i += G) cY[i] = io.Y[(long long)i * io.n + lc];
+        for (int i = l; i < S; i += G) cY[i] = __ldcg(io.Y + (long long)i * io.n + lc);
       else
-        for (int i = l; i < S; i += G) cY[i] = io.Y[lc * S + i];
+        for (int i = l; i < S; i += G) cY[i] = __ldcg(io.Y + lc * S + i);
       for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0;  // Eq. 11
     }
     __syncwarp();
-    if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
+    if (!__any_sync(0xffffffffu, st.cell >= 0)) {
+      if (!L.serve) break;
+      // serving: wait for published work; bounded by stop and the grid-wide idle exit
+      if (serve_idle(L, idle_since, idle_committed)) break;
+      __nanosleep(idle_sleep);
+      idle_sleep = min(2u * idle_sleep, 32000u);
+      serve_skip = 0;
+      continue;
+    }
+    idle_since = 0;
+    idle_sleep = 1000u;
     const int outcome = step_fp64<G>(L, tb, cY, cC, cG, cH, cQ, cHist, cRof, l, st);
     if (st.cell >= 0 && outcome >= 0) {
       const CellIO io = cell_io(L, st.b);
@@ -265,6 +298,7 @@ __global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
         for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = cY[i];
       else
         for (int i = l; i < S; i += G) io.Y_out[c * S + i] = cY[i];
+      if (L.serve) serve_cell_done<G>(L, st.b, io.n, l);
       st.cell = -1;
     }
   }

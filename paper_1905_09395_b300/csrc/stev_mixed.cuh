@@ -63,21 +63,20 @@ __device__ __forceinline__ double log1p_small(double u) {
 }
 
 // MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
-// (Sec. 3), evaluated by the cell's warp (G == 32) into cTh (cp/R, then H/R),
-// whenever T is inside the network's training range; outside it, and for G/RT
-// always, the NASA-7 polynomials are used.
+// (Sec. 3) whenever T is inside its training range; outside it, and for G/RT
+// always, the NASA-7 polynomials are used.  The CTA evaluates the network for
+// all its cells at once (stev_mixed_net_kernel); this cell's outputs (cp/R,
+// then H/R) are in cTh once named barrier 2 has completed, which the step
+// waits for (net_bar = the CTA's thread count) only where it first needs them,
+// after the rates; net_bar = 0 when the caller evaluated them itself.
 template <int G, bool MLP>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
                                           float* cYf, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
-                                          CellState& st, __nv_bfloat16* a1buf, float* cTh) {
+                                          CellState& st, const float* cTh, int net_bar) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
-  bool use_net = false;
-  if (MLP) {
-    use_net = T >= kMlpTLow && T <= kMlpTHigh;  // warp-uniform: one cell per warp
-    if (use_net) mlp_eval_row(L.mlp, ((float)T - kTMid) / kTHalf, a1buf, cTh, L.mlp_needed);
-  }
+  const bool use_net = MLP && T >= kMlpTLow && T <= kMlpTHigh;  // one cell per warp
   const double lnT = st.lnT;        // FP64: feeds G/RT
   const double invT = 1.0 / T;
   const float Tf = (float)T;
@@ -99,16 +98,12 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const float* b = spf + (lo ? SPF_LOW : SPF_HIGH);
     const double* bd = sp + (lo ? SP_LOW : SP_HIGH);
     const float Yi = cYf[i];
-    float cpR;
-    if (MLP && use_net) {
-      cpR = cTh[i];
-    } else {
-      cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf, b[BF_A1]), Tf,
-                 b[BF_A0]);
+    if (!use_net) {
+      const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf,
+                                  b[BF_A1]), Tf, b[BF_A0]);
+      cpp = fmaf(Yi * cpR, spf[SPF_INVW], cpp);
     }
-    if (MLP && use_net && L.mlp_h) {
-      cH[i] = cTh[S + i] * invTf;  // the network gives H/R
-    } else {
+    if (!(use_net && L.mlp_h)) {
       const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
       cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
     }
@@ -116,12 +111,12 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const double g2 = (fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T) * kLog2e;
     const float ghi = (float)g2;
     cG2[i] = make_float2(ghi, (float)(g2 - (double)ghi));  // g2 == hi + lo to ~2^-48
-    cpp = fmaf(Yi * cpR, spf[SPF_INVW], cpp);
     const float y = fmaxf(Yi, 0.0f);
     const float ys = (L.alpha > 0.0) ? y * __fdividef(y, (float)L.alpha + y) : y;
     cC[i] = rho * ys * spf[SPF_INVW];
   }
-  const float cpsum = group_sum<G>(cpp);
+  float cpsum = 0.0f;
+  if (!MLP) cpsum = group_sum<G>(cpp);
   __syncwarp();
 
   // rates of progress: kf = 2^(lg2 A + beta lg2 T - Ea/R log2e / T) (FP32);
@@ -172,6 +167,18 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     cQ[r] = q * rof;
   }
   __syncwarp();
+
+  if (MLP) {
+    // the network's outputs for this cell (the CTA evaluated them meanwhile)
+    if (net_bar) asm volatile("bar.sync 2, %0;" ::"r"(net_bar) : "memory");
+    if (use_net) {
+      for (int i = l; i < S; i += G) {
+        cpp = fmaf(cYf[i] * cTh[i], tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+        if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
+      }
+    }
+    cpsum = group_sum<G>(cpp);
+  }
 
   // production rates, dY/dt, dT/dt terms and the limiter (FP32)
   const float invRho = 1.0f / rho;
@@ -271,10 +278,35 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   return -1;
 }
 
-template <int G, bool MLP>
-__global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
-    stev_mixed_kernel(Launch L) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Shared-memory pointers of one resident cell of the mixed kernels.
+struct MixedCell {
+  double* Y;
+  float2* G2;
+  float* C;
+  float* H;
+  float* Yf;  // float shadow of Y for the FP32 parts
+  float* Q;
+  float* Hist;
+  float* Rof;
+  float* Th;  // network outputs (network kernel only)
+};
+
+__device__ __forceinline__ MixedCell mixed_cell(const Launch& L, unsigned char* base) {
+  MixedCell c;
+  c.Y = reinterpret_cast<double*>(base);
+  c.G2 = reinterpret_cast<float2*>(c.Y + L.S);
+  c.C = reinterpret_cast<float*>(c.G2 + L.S);
+  c.H = c.C + L.S;
+  c.Yf = c.H + L.S;
+  c.Q = c.Yf + L.S;
+  c.Hist = c.Q + L.R;
+  c.Rof = c.Hist + L.dft_n * L.Rrev;
+  c.Th = c.Rof + L.Rrev;
+  return c;
+}
+
+// Stages the mechanism tables of the mixed kernels in shared memory.
+__device__ __forceinline__ TablesF stage_tables_mixed(const Launch& L, unsigned char* smem_raw) {
   const int S = L.S, R = L.R;
   double* s_sp = reinterpret_cast<double*>(smem_raw);
   float4* s_rxf = reinterpret_cast<float4*>(s_sp + S * SP_STRIDE);
@@ -291,30 +323,10 @@ __global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
   for (int t = threadIdx.x; t <= S; t += blockDim.x) s_gptr[t] = L.g_ptr[t];
   for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
   __syncthreads();
-  const TablesF tb{s_sp, s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw};
+  return TablesF{s_sp, s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw};
+}
 
-  const int group = threadIdx.x / G;
-  const int l = threadIdx.x % G;
-  const size_t tables = table_smem_bytes_mixed(S, R, L.n_gather, L.n_hi_bins, L.dft_n);
-  const size_t cell_bytes = cell_smem_bytes_mixed(S, R, L.Rrev, L.dft_n, MLP);
-  unsigned char* base = smem_raw + tables + (size_t)group * cell_bytes;
-  double* cY = reinterpret_cast<double*>(base);
-  float2* cG2 = reinterpret_cast<float2*>(cY + S);
-  float* cC = reinterpret_cast<float*>(cG2 + S);
-  float* cH = cC + S;
-  float* cYf = cH + S;  // float shadow of Y for the FP32 parts
-  float* cQ = cYf + S;
-  float* cHist = cQ + R;
-  float* cRof = cHist + L.dft_n * L.Rrev;
-  // thermo network buffers (MLP only): 64 BF16 of layer-1 output, 2S outputs
-  __nv_bfloat16* a1buf = reinterpret_cast<__nv_bfloat16*>(cRof + L.Rrev);
-  float* cTh = reinterpret_cast<float*>(a1buf + kHid);
-  for (int i = l; i < S; i += G) {
-    cY[i] = 0.0;
-    cYf[i] = 0.0f;
-  }
-
-  const unsigned long long n = (unsigned long long)L.n_cells;
+__device__ __forceinline__ CellState idle_cell_state() {
   CellState st;
   st.cell = -1;
   st.T = 1000.0;
@@ -326,48 +338,229 @@ __global__ void __launch_bounds__(MLP ? kMaxBlockMixedNet : kMaxBlockMixed, 1)
   st.it = 0;
   st.nhist = 0;
   st.lnT = log(1000.0);
+  return st;
+}
+
+// Claims cell c for the group: finds its batch or request and loads its state.
+template <int G>
+__device__ __forceinline__ void load_mixed_cell(const Launch& L, long long c, int l,
+                                                MixedCell& cs, CellState& st, float& Pf) {
+  if (L.serve) {
+    st.b = serve_find_slot(L, c, st.lc);
+    if (st.b < 0) {  // dropped: counted in ctl->dropped
+      st.b = 0;
+      return;
+    }
+  } else {
+    st.b = find_batch(L, c);
+    st.lc = L.nb > 0 ? c - L.boff[st.b] : c;
+  }
+  const int S = L.S;
+  const CellIO io = cell_io(L, st.b);
+  const long long lc = st.lc;
+  st.cell = c;
+  st.T = __ldcg(io.T + lc);  // L1 bypass: serving reuses these addresses
+  st.P = __ldcg(io.P + lc);
+  st.dt = io.dt;
+  st.t_rem = io.dt;
+  st.it = 0;
+  st.nhist = 0;
+  st.lnT = log(st.T);
+  Pf = (float)st.P;
+  if (L.y_soa)
+    for (int i = l; i < S; i += G) cs.Y[i] = __ldcg(io.Y + (long long)i * io.n + lc);
+  else
+    for (int i = l; i < S; i += G) cs.Y[i] = __ldcg(io.Y + lc * S + i);
+  for (int i = l; i < S; i += G) cs.Yf[i] = (float)cs.Y[i];
+  for (int w = l; w < L.Rrev; w += G) cs.Rof[w] = 1.0f;
+}
+
+// Writes a finished cell's outputs and frees the group.
+template <int G>
+__device__ __forceinline__ void store_mixed_cell(const Launch& L, int l, MixedCell& cs,
+                                                 CellState& st, int outcome) {
+  const int S = L.S;
+  const CellIO io = cell_io(L, st.b);
+  const long long c = st.lc;
+  if (l == 0) {
+    io.T_out[c] = st.T;
+    io.iters[c] = st.it;
+    io.status[c] = (unsigned char)outcome;
+  }
+  if (L.y_soa)
+    for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = cs.Y[i];
+  else
+    for (int i = l; i < S; i += G) io.Y_out[c * S + i] = cs.Y[i];
+  if (L.serve) serve_cell_done<G>(L, st.b, io.n, l);
+  st.cell = -1;
+}
+
+// Mixed-precision persistent kernel, NASA-7 thermo: lane groups of G lanes,
+// one cell each, refilled in place (Sec. 2.4).
+template <int G>
+__global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = L.S;
+  const TablesF tb = stage_tables_mixed(L, smem_raw);
+
+  const int group = threadIdx.x / G;
+  const int l = threadIdx.x % G;
+  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, false);
+  MixedCell cs = mixed_cell(L, smem_raw + tables + (size_t)group * cell_bytes);
+  for (int i = l; i < S; i += G) {
+    cs.Y[i] = 0.0;
+    cs.Yf[i] = 0.0f;
+  }
+
+  const unsigned long long n = (unsigned long long)L.n_cells;
+  CellState st = idle_cell_state();
   float Pf = (float)kPatm;
+  unsigned long long idle_since = 0;  // serving: when this warp last ran out of work
+  bool idle_committed = false;        // serving: counted in ctl->idle_warps
+  unsigned idle_sleep = 1000u;        // serving: ns between looks while idle
+  int serve_skip = 0;                 // serving: steps before the next look
   bool exhausted = false;
   while (true) {
-    const long long c = refill<G>(L.counter, n, st.cell < 0, exhausted);
-    if (c >= 0) {
-      st.b = find_batch(L, c);
-      const CellIO io = cell_io(L, st.b);
-      st.lc = L.nb > 0 ? c - L.boff[st.b] : c;
-      const long long lc = st.lc;
-      st.cell = c;
-      st.T = io.T[lc];
-      st.P = io.P[lc];
-      st.dt = io.dt;
-      st.t_rem = io.dt;
-      st.it = 0;
-      st.nhist = 0;
-      st.lnT = log(st.T);
-      Pf = (float)st.P;
-      if (L.y_soa)
-        for (int i = l; i < S; i += G) cY[i] = io.Y[(long long)i * io.n + lc];
-      else
-        for (int i = l; i < S; i += G) cY[i] = io.Y[lc * S + i];
-      for (int i = l; i < S; i += G) cYf[i] = (float)cY[i];
-      for (int w = l; w < L.Rrev; w += G) cRof[w] = 1.0f;
+    long long c = -1;
+    if (!L.serve) {
+      c = refill<G>(L.counter, n, st.cell < 0, exhausted);
+    } else if (serve_skip > 0) {
+      --serve_skip;  // nothing was ready recently: look again in a few steps
+    } else if (idle_committed) {
+      // counted idle: the idle path counts the warp out before it claims
+    } else {
+      bool none_ready;
+      c = serve_refill<G>(L, st.cell < 0, none_ready);
+      if (none_ready) serve_skip = 32;
     }
+    if (c >= 0) load_mixed_cell<G>(L, c, l, cs, st, Pf);
     __syncwarp();
-    if (!__any_sync(0xffffffffu, st.cell >= 0)) break;
-    const int outcome =
-        step_mixed<G, MLP>(L, tb, cY, cYf, cG2, cC, cH, cQ, cHist, cRof, Pf, l, st, a1buf, cTh);
-    if (st.cell >= 0 && outcome >= 0) {
-      const CellIO io = cell_io(L, st.b);
-      const long long c = st.lc;
-      if (l == 0) {
-        io.T_out[c] = st.T;
-        io.iters[c] = st.it;
-        io.status[c] = (unsigned char)outcome;
-      }
-      if (L.y_soa)
-        for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = cY[i];
-      else
-        for (int i = l; i < S; i += G) io.Y_out[c * S + i] = cY[i];
-      st.cell = -1;
+    if (!__any_sync(0xffffffffu, st.cell >= 0)) {
+      if (!L.serve) break;
+      // serving: wait for published work; bounded by stop and the grid-wide idle exit
+      if (serve_idle(L, idle_since, idle_committed)) break;
+      __nanosleep(idle_sleep);
+      idle_sleep = min(2u * idle_sleep, 32000u);
+      serve_skip = 0;
+      continue;
+    }
+    idle_since = 0;
+    idle_sleep = 1000u;
+    const int outcome = step_mixed<G, false>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
+                                             cs.Hist, cs.Rof, Pf, l, st, nullptr, 0);
+    if (st.cell >= 0 && outcome >= 0) store_mixed_cell<G>(L, l, cs, st, outcome);
+  }
+}
+
+// Mixed-precision persistent kernel with the thermo network (Sec. 3): one
+// cell per warp (G = 32), the CTA's warps in lockstep so that the network is
+// evaluated for 16 cells per MMA tile instead of one.  Each iteration:
+//   1. every warp refills if it has no cell, publishes its cell's scaled T
+//      and counts itself in this iteration's counter (staying, live);
+//   2. warp 16k (the evaluator of tile k) waits on named barrier 1 for every
+//      warp's T, evaluates the network for rows 16k..16k+15 into those cells'
+//      output rows and arrives on named barrier 2; the other warps only
+//      arrive on barrier 1 and go on with their step;
+//   3. a live warp takes its step, waiting on barrier 2 only where cp/R is
+//      first needed (after its rates); a warp without a cell waits on it
+//      directly;
+//   4. every warp reads the iteration's counter: the CTA leaves together when
+//      no warp stays (no cell and, serving, the grid-wide exit reached), and
+//      sleeps while no warp has a cell.
+// Counters rotate over three slots: the evaluator of tile 0 clears the slot
+// of iteration i + 2 after barrier 1 of iteration i, when every reader of
+// that slot (iteration i - 1) has passed and no writer (iteration i + 2) can
+// have started.
+__global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(Launch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = L.S;
+  const TablesF tb = stage_tables_mixed(L, smem_raw);
+  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5, nthreads = blockDim.x;
+  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, true);
+  unsigned char* cells = smem_raw + tables;
+  MixedCell cs = mixed_cell(L, cells + (size_t)warp * cell_bytes);
+  const int tiles = (nwarps + 15) / 16;
+  float* sT = reinterpret_cast<float*>(cells + (size_t)nwarps * cell_bytes);
+  __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sT + tiles * 16);
+  int* s_count = reinterpret_cast<int*>(act + tiles * 16 * kNetActLd);
+  // cell r's output row is at a fixed offset in its cell block: rows cell_bytes apart
+  const int out_ld = (int)(cell_bytes / sizeof(float));
+  for (int i = l; i < S; i += 32) {
+    cs.Y[i] = 0.0;
+    cs.Yf[i] = 0.0f;
+  }
+  if (threadIdx.x < 3) s_count[threadIdx.x] = 0;
+  if (threadIdx.x < tiles * 16) sT[threadIdx.x] = 0.0f;
+  __syncthreads();
+  const bool evaluator = (warp & 15) == 0;
+  const int tile = warp >> 4;
+
+  const unsigned long long n = (unsigned long long)L.n_cells;
+  CellState st = idle_cell_state();
+  float Pf = (float)kPatm;
+  unsigned long long idle_since = 0;
+  bool idle_committed = false;
+  unsigned idle_sleep = 1000u;
+  int serve_skip = 0;
+  bool exhausted = false, leaving = false;
+  int slot = 0;  // this iteration's counter (rotates 0, 1, 2)
+  while (true) {
+    long long c = -1;
+    if (leaving) {
+      // decided to leave: claims nothing, waits for the rest of the CTA
+    } else if (!L.serve) {
+      c = refill<32>(L.counter, n, st.cell < 0, exhausted);
+    } else if (serve_skip > 0) {
+      --serve_skip;
+    } else if (!idle_committed) {
+      bool none_ready;
+      c = serve_refill<32>(L, st.cell < 0, none_ready);
+      if (none_ready) serve_skip = 32;
+    }
+    if (c >= 0) load_mixed_cell<32>(L, c, l, cs, st, Pf);
+    __syncwarp();
+    const bool live = st.cell >= 0;  // warp-uniform
+    if (!live && !leaving) {
+      if (!L.serve) leaving = exhausted;
+      else leaving = serve_idle(L, idle_since, idle_committed);
+    }
+    if (live) idle_since = 0;
+    int* cnt = s_count + slot;
+    if (l == 0) {
+      if (live || !leaving) atomicAdd(cnt, live ? 0x10001 : 1);  // staying (+ live << 16)
+      sT[warp] = live ? ((float)st.T - kTMid) / kTHalf : 0.0f;
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (evaluator) {
+      asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+      if (warp == 0 && l == 0) s_count[slot == 0 ? 2 : slot - 1] = 0;  // slot of iteration + 2
+      mlp_eval_warp16(L.mlp, sT + tile * 16, act + tile * 16 * kNetActLd,
+                      cs.Th, out_ld, min(16, nwarps - tile * 16), 0, L.mlp_needed);
+      __threadfence_block();
+      asm volatile("bar.arrive 2, %0;" ::"r"(nthreads) : "memory");
+    } else {
+      asm volatile("bar.arrive 1, %0;" ::"r"(nthreads) : "memory");
+    }
+    if (live) {
+      idle_sleep = 1000u;
+      const int outcome = step_mixed<32, true>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
+                                               cs.Hist, cs.Rof, Pf, l, st, cs.Th,
+                                               evaluator ? 0 : nthreads);
+      if (outcome >= 0) store_mixed_cell<32>(L, l, cs, st, outcome);
+    } else if (!evaluator) {
+      asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
+    }
+    const int v = *(volatile int*)cnt;  // complete: every warp counted before barrier 1
+    slot = slot == 2 ? 0 : slot + 1;
+    if ((v & 0xFFFF) == 0) break;       // nobody stays: the CTA leaves together
+    if ((v >> 16) == 0 && L.serve) {    // no cell in the CTA: sleep between looks
+      serve_skip = 0;
+      __nanosleep(idle_sleep);
+      idle_sleep = min(2u * idle_sleep, 32000u);
     }
   }
 }

@@ -68,9 +68,12 @@ __global__ void mlp_targets_kernel(const double* __restrict__ sp_tab, int S,
   o[2 * S + i] = (float)(hRT - gRT);
 }
 
-// column sums and sums of squares (FP64 accumulation) for standardisation
+// Column sums and sums of squares (FP64) for standardisation: block
+// (x, col) writes its partial pair to part[(col * gridDim.x + x) * 2]; the
+// host adds the partials in order (no atomics: the result is reproducible).
 __global__ void mlp_moments_kernel(const float* __restrict__ v, long long n, int m,
-                                   double* __restrict__ sum, double* __restrict__ sum2) {
+                                   double* __restrict__ part) {
+  __shared__ double wa[32], wb[32];
   const int col = blockIdx.y;
   double a = 0.0, b = 0.0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
@@ -84,8 +87,19 @@ __global__ void mlp_moments_kernel(const float* __restrict__ v, long long n, int
     b += __shfl_xor_sync(0xffffffffu, b, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(sum + col, a);
-    atomicAdd(sum2 + col, b);
+    wa[threadIdx.x >> 5] = a;
+    wb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += wa[w];
+      sb += wb[w];
+    }
+    double* o = part + ((size_t)col * gridDim.x + blockIdx.x) * 2;
+    o[0] = sa;
+    o[1] = sb;
   }
 }
 
@@ -102,12 +116,15 @@ __global__ void mlp_standardise_kernel(float* __restrict__ v, long long n, int m
 // One CTA of kMlpTile threads: thread s owns sample s of the tile.  Shared
 // memory: the parameters, then feature-major activations a1, a2, dz1, dz2
 // [64][tile+1] and dy [n_out][tile+1] (the +1 keeps rows on distinct banks).
-// Adds d loss / d params to grad and the tile's sum of squared errors to
-// loss_sum; the loss is the mean over n_total samples and n_out outputs.
+// Writes the tile's d loss / d params to part[blockIdx.x][params] and its sum
+// of squared errors to loss_part[blockIdx.x] (the loss is the mean over
+// n_total samples and n_out outputs); mlp_adam_kernel / mlp_sum_kernel add
+// the tiles in order, so training is reproducible run to run.
 __global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
     const float* __restrict__ params, int n_out, const double* __restrict__ T,
-    const float* __restrict__ target, long long n, long long n_total, float* __restrict__ grad,
-    double* __restrict__ loss_sum) {
+    const float* __restrict__ target, long long n, long long n_total, float* __restrict__ part,
+    double* __restrict__ loss_part) {
+  __shared__ double se_w[kMlpTile / 32];
   extern __shared__ __align__(16) float sm[];
   const MlpOffsets off = mlp_offsets(n_out);
   float* P = sm;
@@ -156,8 +173,13 @@ __global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
     z1[j * ld + s] = acc * (1.0f - a * a);
   }
   for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, se);
+  if ((threadIdx.x & 31) == 0) se_w[threadIdx.x >> 5] = se;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kMlpTile / 32; ++w) t += se_w[w];
+    loss_part[blockIdx.x] = t;
+  }
 
   // weight gradients: sums over the tile's samples
   const int nt = (int)min((long long)kMlpTile, n - s0);
@@ -182,8 +204,25 @@ __global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
       const int o = k - off.b3;
       for (int q = 0; q < nt; ++q) acc += dy[o * ld + q];
     }
-    atomicAdd(grad + k, acc);
+    part[(size_t)blockIdx.x * off.total + k] = acc;
   }
+}
+
+// grad[k] = sum over tiles of part[tile][k], tiles in order; thread 0 also
+// adds the tiles' squared errors, in order, to *loss_acc.
+__global__ void mlp_sum_kernel(const float* __restrict__ part, int tiles, int n,
+                               const double* __restrict__ loss_part, float* __restrict__ grad,
+                               double* __restrict__ loss_acc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) {
+    double t = 0.0;
+    for (int b = 0; b < tiles; ++b) t += loss_part[b];
+    *loss_acc += t;
+  }
+  if (k >= n) return;
+  float g = 0.0f;
+  for (int b = 0; b < tiles; ++b) g += part[(size_t)b * n + k];
+  grad[k] = g;
 }
 
 __host__ __device__ inline size_t mlp_grad_smem_bytes(int n_out) {
@@ -191,19 +230,27 @@ __host__ __device__ inline size_t mlp_grad_smem_bytes(int n_out) {
          sizeof(float);
 }
 
-// Adam (Kingma & Ba 2015) on every parameter; clears the gradient.
-__global__ void mlp_adam_kernel(float* __restrict__ p, float* __restrict__ g,
+// Adam (Kingma & Ba 2015) on every parameter, the gradient being the sum of
+// the minibatch's tile partials (in tile order); thread 0 adds the tiles'
+// squared errors to *loss_acc.
+__global__ void mlp_adam_kernel(float* __restrict__ p, const float* __restrict__ part, int tiles,
+                                const double* __restrict__ loss_part, double* __restrict__ loss_acc,
                                 float* __restrict__ m1, float* __restrict__ m2, int n, float lr,
                                 float beta1, float beta2, float eps, float bc1, float bc2) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) {
+    double t = 0.0;
+    for (int b = 0; b < tiles; ++b) t += loss_part[b];
+    *loss_acc += t;
+  }
   if (k >= n) return;
-  const float gk = g[k];
+  float gk = 0.0f;
+  for (int b = 0; b < tiles; ++b) gk += part[(size_t)b * n + k];
   const float a = beta1 * m1[k] + (1.0f - beta1) * gk;
   const float b = beta2 * m2[k] + (1.0f - beta2) * gk * gk;
   m1[k] = a;
   m2[k] = b;
   p[k] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
-  g[k] = 0.0f;
 }
 
 // ------------------------------------------------------------- inference
@@ -309,75 +356,6 @@ __device__ void mlp_eval_warp16(const MlpInfer& w, const float* t16, __nv_bfloat
     if (g + 8 < n_rows) {
       if (c0ok) out[(g + 8) * out_ld + c - o_begin] = fmaf(d[2], s0, m0);
       if (c1ok) out[(g + 8) * out_ld + c + 1 - o_begin] = fmaf(d[3], s1, m1);
-    }
-  }
-  __syncwarp();
-}
-
-// The network at one temperature per warp, for the solver: row 0 of a 16-row
-// MMA tile (the other rows are zero).  a1buf is a warp-private shared buffer
-// of 64 BF16; out receives the values of outputs [0, n_needed) (n_needed a
-// multiple of 8, at most n_out).  Layer 2's row-0 results come back in lanes
-// 0-3 exactly where layer 3's A fragment needs them, so only layer 1 passes
-// through shared memory.
-__device__ void mlp_eval_row(const MlpInfer& w, float t, __nv_bfloat16* a1buf, float* out,
-                             int n_needed) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, tg = lane & 3;
-  {
-    const int j = lane * 2;
-    const float h0 = tanh_approx(fmaf(w.W1[j], t, w.b1[j]));
-    const float h1 = tanh_approx(fmaf(w.W1[j + 1], t, w.b1[j + 1]));
-    *reinterpret_cast<unsigned*>(a1buf + j) = pack_bf16(h0, h1);
-  }
-  __syncwarp();
-  float acc[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    acc[nt][0] = w.b2[nt * 8 + tg * 2];
-    acc[nt][1] = w.b2[nt * 8 + tg * 2 + 1];
-    acc[nt][2] = 0.0f;
-    acc[nt][3] = 0.0f;
-  }
-#pragma unroll
-  for (int ks = 0; ks < 4; ++ks) {
-    unsigned a[4];
-    a[0] = g == 0 ? *reinterpret_cast<const unsigned*>(a1buf + ks * 16 + tg * 2) : 0u;
-    a[1] = 0u;
-    a[2] = g == 0 ? *reinterpret_cast<const unsigned*>(a1buf + ks * 16 + 8 + tg * 2) : 0u;
-    a[3] = 0u;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const __nv_bfloat16* wr = w.W2 + (nt * 8 + g) * kHid + ks * 16 + tg * 2;
-      unsigned b[2];
-      b[0] = __ldg(reinterpret_cast<const unsigned*>(wr));
-      b[1] = __ldg(reinterpret_cast<const unsigned*>(wr + 8));
-      mma_bf16_16816(acc[nt], a, b);
-    }
-  }
-  unsigned a3[4][4];
-#pragma unroll
-  for (int ks = 0; ks < 4; ++ks) {
-    a3[ks][0] = g == 0 ? pack_bf16(tanh_approx(acc[2 * ks][0]), tanh_approx(acc[2 * ks][1])) : 0u;
-    a3[ks][1] = 0u;
-    a3[ks][2] = g == 0 ? pack_bf16(tanh_approx(acc[2 * ks + 1][0]), tanh_approx(acc[2 * ks + 1][1]))
-                       : 0u;
-    a3[ks][3] = 0u;
-  }
-  for (int o0 = 0; o0 < n_needed; o0 += 8) {
-    const int c = o0 + tg * 2;
-    float d[4] = {w.b3[c], w.b3[c + 1], 0.0f, 0.0f};
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const __nv_bfloat16* wr = w.W3 + (o0 + g) * kHid + ks * 16 + tg * 2;
-      unsigned b[2];
-      b[0] = __ldg(reinterpret_cast<const unsigned*>(wr));
-      b[1] = __ldg(reinterpret_cast<const unsigned*>(wr + 8));
-      mma_bf16_16816(d, a3[ks], b);
-    }
-    if (g == 0) {
-      out[c] = fmaf(d[0], w.stdv[c], w.mean[c]);
-      out[c + 1] = fmaf(d[1], w.stdv[c + 1], w.mean[c + 1]);
     }
   }
   __syncwarp();

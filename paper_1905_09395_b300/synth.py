@@ -300,3 +300,22 @@ def uneven_case(scale: float = 1.0, seed: int = 3):
 def uneven_batch_sizes(n_batches: int = 64, lo: int = 1000, hi: int = 256000, seed: int = 3):
     rng = np.random.default_rng(seed + 104729)
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_batches)).astype(np.int64)
+
+
+def serving_requests(duration: float = 10.0, rate: float = 200.0, lo: int = 1000,
+                     hi: int = 512 * 1024, n_mechanisms: int = 2, seed: int = 4):
+    """Seeded request stream of the serving workload: Poisson arrivals at
+    `rate` per second over `duration` seconds, sizes log-uniform [lo, hi]
+    cells, each request on a mechanism drawn uniformly from n_mechanisms.
+    Returns a list of (arrival time s, mechanism index, n_cells, pool offset),
+    the offset placing the request's cells inside a pool of `hi` cells."""
+    rng = np.random.default_rng(seed + 15485863)
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return out
+        mi = int(rng.integers(n_mechanisms))
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        off = int(rng.integers(0, hi - n + 1))
+        out.append((t, mi, n, off))

@@ -31,7 +31,10 @@ def _solve(mech, T, P, Y, dt, **opts):
     return out
 
 
-def _check(mech, T0, Y0, gpu, ref, sY, sT, label):
+def _check(mech, T0, Y0, gpu, ref, sY, sT, label, outliers=0.0, outlier_cap=None):
+    """outliers: fraction of well-conditioned cells allowed over the target,
+    each still within outlier_cap = (dY, dT) (for approximations such as the
+    thermo network, whose error is systematic rather than rounding-sized)."""
     To, Yo, it, st = gpu
     rT, rY, rit, rst = ref
     assert (st == rst).all(), "status differs in %d cells" % int((st != rst).sum())
@@ -39,8 +42,12 @@ def _check(mech, T0, Y0, gpu, ref, sY, sT, label):
     dT = np.abs(To - rT)
     well = (sY < WELL_Y) & (sT < WELL_T)
     bad = np.nonzero(well & ((dY > TOL_Y) | (dT > TOL_T)))[0]
-    assert bad.size == 0, "well-conditioned cells over target: %s dY %s dT %s" % (
-        bad[:8], dY[bad[:8]], dT[bad[:8]])
+    assert bad.size <= outliers * well.sum(), (
+        "well-conditioned cells over target: %d, e.g. %s dY %s dT %s"
+        % (bad.size, bad[:8], dY[bad[:8]], dT[bad[:8]]))
+    if bad.size:
+        assert np.all(dY[bad] <= outlier_cap[0]) and np.all(dT[bad] <= outlier_cap[1]), (
+            "outliers beyond their cap: dY %s dT %s" % (dY[bad].max(), dT[bad].max()))
     assert np.all(dY <= np.maximum(TOL_Y + 100 * sY, 2e-3)), "Y beyond validity bound"
     H0, _, _ = _enthalpy(mech, T0, Y0)
     Hg, cpg, hWg = _enthalpy(mech, To, Yo)
@@ -52,10 +59,10 @@ def _check(mech, T0, Y0, gpu, ref, sY, sT, label):
     # relative per step), so sum Y drifts by far less than the target
     np.testing.assert_allclose(Yo.sum(axis=1), Y0.sum(axis=1), rtol=0, atol=1e-6)
     within = np.mean((dY <= TOL_Y) & (dT <= TOL_T))
-    print("%s: well-conditioned %.3f, within target %.4f, max dY %.3g (well %.3g), max dT %.3g,"
-          " iteration match %.3f" % (label, well.mean(), within, dY.max(),
-                                     dY[well].max() if well.any() else 0, dT.max(),
-                                     np.mean(it == rit)))
+    print("%s: well-conditioned %.3f, within target %.4f (well-conditioned %.4f), max dY %.3g"
+          " (well %.3g), max dT %.3g, iteration match %.3f"
+          % (label, well.mean(), within, 1.0 - bad.size / max(well.sum(), 1), dY.max(),
+             dY[well].max() if well.any() else 0, dT.max(), np.mean(it == rit)))
     return within
 
 

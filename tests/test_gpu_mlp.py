@@ -37,6 +37,21 @@ def test_gradients_match_fp64_reference():
     m.close()
 
 
+def test_training_is_reproducible():
+    # gradients are summed over tiles in a fixed order: same inputs, same network
+    mech = synth.small_mechanism()
+    T = np.random.default_rng(3).uniform(300.0, 3000.0, size=100_000)
+    runs = []
+    for _ in range(2):
+        m = Mechanism(mech)
+        hist = m.mlp_train(T, epochs=3, batch=4096, lr=2e-3, seed=5)
+        runs.append((hist, m.mlp_params()))
+        m.close()
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    for a, b in zip(runs[0][1], runs[1][1]):
+        np.testing.assert_array_equal(a, b)
+
+
 @pytest.fixture(scope="module")
 def trained():
     mech = synth.scale_mechanism()
