@@ -307,6 +307,12 @@ stev_status stev_server_stop(stev_server *srv, double timeout_s);
  * device buffers are not freed.  NULL is a no-op. */
 stev_status stev_server_destroy(stev_server *srv, double timeout_s);
 
+/* Cell-steps of this mechanism's network solves so far that took the
+ * polynomials because the network's answer did not arrive within the step's
+ * bounded wait (about 2^20 sleeps; never expected).  Synchronous; -1 if the
+ * device read fails. */
+long long stev_mlp_stalls(const stev_mechanism *mech);
+
 /* Number of resident solver slots (cells in flight) of the persistent kernel
  * on the current device for this mechanism and its options. */
 long stev_resident_slots(const stev_mechanism *mech);

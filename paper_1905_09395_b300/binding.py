@@ -30,7 +30,7 @@ EXPORTS = (
     "stev_mlp_num_params", "stev_mlp_train", "stev_mlp_set_params", "stev_mlp_get_params",
     "stev_mlp_loss_grad", "stev_mlp_eval", "stev_solve_batched",
     "stev_server_create", "stev_server_submit", "stev_server_poll", "stev_server_get_stats",
-    "stev_server_clock", "stev_server_stop", "stev_server_destroy",
+    "stev_server_clock", "stev_server_stop", "stev_server_destroy", "stev_mlp_stalls",
 )
 
 
@@ -124,6 +124,8 @@ def lib():
         L.stev_server_stop.restype = I
         L.stev_server_destroy.argtypes = [P, D]
         L.stev_server_destroy.restype = I
+        L.stev_mlp_stalls.argtypes = [P]
+        L.stev_mlp_stalls.restype = ctypes.c_longlong
         L.stev_resident_slots.argtypes = [P]
         L.stev_resident_slots.restype = LNG
         L.stev_destroy.argtypes = [P]
@@ -196,6 +198,11 @@ class Mechanism:
                 raise KeyError(k)
             setattr(o, k, v)
         _check(lib().stev_mechanism_set_options(self._h, ctypes.byref(o)))
+
+    @property
+    def mlp_stalls(self) -> int:
+        """Network answers that timed out (the step took the polynomials); expected 0."""
+        return int(lib().stev_mlp_stalls(self._h))
 
     @property
     def resident_slots(self) -> int:

@@ -67,6 +67,8 @@ struct stev_mechanism {
   int G = 32;              // lanes per cell
   int block = 0, grid = 0; // threads per CTA, CTAs
   int per_sm = 0, sms = 0;  // resident CTAs per SM, SMs
+  int cells = 0;            // resident cells per CTA
+  unsigned long long* d_net_stalls = nullptr;  // network answers that timed out
   size_t smem = 0;
   long long nslots = 0;    // cells resident at once
   unsigned long long* d_counter = nullptr;
@@ -132,7 +134,7 @@ static stev_status check_options(const stev_options* o) {
 static void free_mech(stev_mechanism* m) {
   void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
                   m->d_twf, m->d_counter, m->d_mlp_params, m->d_mlp_W2, m->d_mlp_W3, m->d_mlp_misc,
-                  m->d_bdesc, m->d_boff,
+                  m->d_bdesc, m->d_boff, m->d_net_stalls,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -185,27 +187,35 @@ static stev_status configure(stev_mechanism* m) {
   const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n, net)
                             : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
   const size_t limit = prop.sharedMemPerBlockOptin;
-  // the network kernel adds per-CTA buffers (sized here for its largest CTA)
-  const size_t extra = net ? net_cta_smem_bytes(kMaxBlockMixedNet / 32) : 0;
+  // the network kernel adds an evaluator warp and per-CTA buffers (sized here
+  // for its largest CTA)
+  const int max_cells = net ? kMaxBlockMixedNet / 32 - 1 : (mixed ? kMaxBlockMixed : kMaxBlock) / G;
+  const size_t extra = net ? net_cta_smem_bytes(max_cells) : 0;
   if (tables + extra + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
   int cells = (int)((limit - tables - extra) / cell);
-  cells = std::min(cells, (mixed ? (net ? kMaxBlockMixedNet : kMaxBlockMixed) : kMaxBlock) / G);
+  cells = std::min(cells, max_cells);
   const int per_warp = 32 / G;
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
   const size_t smem = tables + (size_t)cells * cell + (net ? net_cta_smem_bytes(cells) : 0);
+  const int block = cells * G + (net ? 32 : 0);
   KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo);
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cells * G, smem));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
   if (per_sm < 1) return fail(STEV_EINVAL, "persistent kernel cannot be resident");
-  m->block = cells * G;
+  m->block = block;
+  m->cells = cells;
   m->per_sm = per_sm;
   m->sms = prop.multiProcessorCount;
   m->grid = per_sm * prop.multiProcessorCount;
   m->smem = smem;
   m->nslots = (long long)m->grid * cells;
   if (!m->d_counter) CUDA_TRY(cudaMalloc(&m->d_counter, sizeof(unsigned long long)));
+  if (!m->d_net_stalls) {
+    CUDA_TRY(cudaMalloc(&m->d_net_stalls, sizeof(unsigned long long)));
+    CUDA_TRY(cudaMemset(m->d_net_stalls, 0, sizeof(unsigned long long)));
+  }
   return STEV_OK;
 }
 
@@ -413,6 +423,13 @@ extern "C" stev_status stev_mechanism_get_options(const stev_mechanism* m, stev_
 
 extern "C" long stev_resident_slots(const stev_mechanism* m) { return m ? (long)m->nslots : 0; }
 
+extern "C" long long stev_mlp_stalls(const stev_mechanism* m) {
+  if (!m || !m->d_net_stalls) return 0;
+  unsigned long long v = 0;
+  if (cudaMemcpy(&v, m->d_net_stalls, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return (long long)v;
+}
+
 static MlpInfer mlp_infer_view(const stev_mechanism* m);
 
 static Launch make_launch(stev_mechanism* m, long long n, double dt) {
@@ -450,6 +467,8 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
     L.mlp_h = m->opt.thermo == STEV_THERMO_MLP_CPH;
     L.mlp_needed = ((L.mlp_h ? 2 : 1) * m->S + 7) / 8 * 8;
   }
+  L.net_cells = m->cells;
+  L.net_stalls = m->d_net_stalls;
   return L;
 }
 
@@ -602,7 +621,7 @@ stev_status serve_config(const stev_mechanism* m, ServeConfig* out) {
   out->S = m->S;
   out->ctas_per_sm = m->per_sm;
   out->sms = m->sms;
-  out->cells_per_cta = m->block / m->G;
+  out->cells_per_cta = m->cells;
   return STEV_OK;
 }
 
@@ -616,7 +635,7 @@ stev_status serve_launch(stev_mechanism* m, ServeCtl* ctl, ServeSlot* slots,
   L.smail = mail;
   L.serve_q = q;
   L.idle_ns = idle_ns;
-  L.serve_warps = grid * (m->block / 32);
+  L.serve_warps = grid * (m->cells * m->G / 32);  // warps holding cells
   L.y_soa = 0;
   CUDA_TRY(cudaMemsetAsync(&ctl->idle_warps, 0, 2 * sizeof(int), s));  // idle_warps, exiting
   select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<grid, m->block, m->smem, s>>>(L);

@@ -33,7 +33,7 @@ constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
 constexpr int kNone = 0xFF;
 constexpr int kMaxBlock = 512;       // threads per CTA of the FP64 persistent kernel
 constexpr int kMaxBlockMixed = 768;  // threads per CTA of the mixed persistent kernel
-constexpr int kMaxBlockMixedNet = 640;  // ... with the thermo network (more registers)
+constexpr int kMaxBlockMixedNet = 672;  // ... with the thermo network: 20 cell warps + 1 evaluator
 
 enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
@@ -117,6 +117,8 @@ struct Launch {
   MlpInfer mlp;           // thermo network (mixed kernel, thermo = MLP)
   int mlp_needed;         // network outputs the solver reads (cp/R [, H/R]), rounded up to 8
   int mlp_h;              // 1: H/RT from the network as well
+  int net_cells;          // network kernel: cell warps per CTA (one more warp evaluates)
+  unsigned long long* net_stalls;  // cell-steps whose network answer timed out (polynomials used)
 };
 
 constexpr double kMlpTLow = 300.0, kMlpTHigh = 3000.0;  // network's training range (K)
@@ -156,12 +158,13 @@ __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, 
 }
 
 // Per-CTA buffers of the network kernel for `cells` resident cells (one per
-// warp): the scaled temperatures (padded to whole 16-row tiles), one 16 x 72
-// BF16 activation tile per 16 cells, and three rotating counters.
+// warp): the published scaled temperatures and request / answer tags (padded
+// to whole 16-row tiles), the evaluator's 16 temperatures and 16 x 72 BF16
+// activation tile, and the count of cell warps still running.
 constexpr int kNetActLd = 64 + 8;
 __host__ __device__ inline size_t net_cta_smem_bytes(int cells) {
-  const int tiles = (cells + 15) / 16;
-  return (size_t)tiles * 16 * 4 + (size_t)tiles * 16 * kNetActLd * 2 + 16;
+  const int rows = (cells + 15) / 16 * 16;
+  return (size_t)rows * 4 * 3 + 16 * 4 + (size_t)16 * kNetActLd * 2 + 16;
 }
 
 }  // namespace stev

@@ -64,16 +64,19 @@ __device__ __forceinline__ double log1p_small(double u) {
 
 // MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
 // (Sec. 3) whenever T is inside its training range; outside it, and for G/RT
-// always, the NASA-7 polynomials are used.  The CTA evaluates the network for
-// all its cells at once (stev_mixed_net_kernel); this cell's outputs (cp/R,
-// then H/R) are in cTh once named barrier 2 has completed, which the step
-// waits for (net_bar = the CTA's thread count) only where it first needs them,
-// after the rates; net_bar = 0 when the caller evaluated them itself.
+// always, the NASA-7 polynomials are used.  The CTA's evaluator warp runs the
+// network for the published temperatures of 16 cells at a time
+// (stev_mixed_net_kernel); this cell's request carries tag net_tag, and its
+// outputs (cp/R, then H/R) are in cTh once *net_ans == net_tag.  The step
+// waits for that only where it first needs them, after the rates, and for at
+// most ~2^20 sleeps; on a timeout it takes the polynomials for this step and
+// counts a stall (never expected).
 template <int G, bool MLP>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
                                           float* cYf, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
-                                          CellState& st, const float* cTh, int net_bar) {
+                                          CellState& st, const float* cTh,
+                                          const volatile int* net_ans, int net_tag) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
   const bool use_net = MLP && T >= kMlpTLow && T <= kMlpTHigh;  // one cell per warp
@@ -169,12 +172,32 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   __syncwarp();
 
   if (MLP) {
-    // the network's outputs for this cell (the CTA evaluated them meanwhile)
-    if (net_bar) asm volatile("bar.sync 2, %0;" ::"r"(net_bar) : "memory");
     if (use_net) {
-      for (int i = l; i < S; i += G) {
-        cpp = fmaf(cYf[i] * cTh[i], tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
-        if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
+      // the network's outputs for this cell (the evaluator ran meanwhile)
+      bool answered = *net_ans == net_tag;
+      for (int k = 0; !answered && k < (1 << 20); ++k) {
+        __nanosleep(32);
+        answered = *net_ans == net_tag;
+      }
+      answered = __all_sync(0xffffffffu, answered);
+      __threadfence_block();
+      if (answered) {
+        for (int i = l; i < S; i += G) {
+          cpp = fmaf(cYf[i] * cTh[i], tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+          if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
+        }
+      } else {
+        if (l == 0) atomicAdd(L.net_stalls, 1ULL);
+        for (int i = l; i < S; i += G) {
+          const float* b = tb.spf + i * SPF_STRIDE + (T < tb.sp[i * SP_STRIDE + SP_TSPLIT] ? SPF_LOW : SPF_HIGH);
+          const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf,
+                                      b[BF_A1]), Tf, b[BF_A0]);
+          cpp = fmaf(cYf[i] * cpR, tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+          if (L.mlp_h) {
+            const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
+            cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+          }
+        }
       }
     }
     cpsum = group_sum<G>(cpp);
@@ -448,56 +471,86 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
     idle_since = 0;
     idle_sleep = 1000u;
     const int outcome = step_mixed<G, false>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
-                                             cs.Hist, cs.Rof, Pf, l, st, nullptr, 0);
+                                             cs.Hist, cs.Rof, Pf, l, st, nullptr, nullptr, 0);
     if (st.cell >= 0 && outcome >= 0) store_mixed_cell<G>(L, l, cs, st, outcome);
   }
 }
 
 // Mixed-precision persistent kernel with the thermo network (Sec. 3): one
-// cell per warp (G = 32), the CTA's warps in lockstep so that the network is
-// evaluated for 16 cells per MMA tile instead of one.  Each iteration:
-//   1. every warp refills if it has no cell, publishes its cell's scaled T
-//      and counts itself in this iteration's counter (staying, live);
-//   2. warp 16k (the evaluator of tile k) waits on named barrier 1 for every
-//      warp's T, evaluates the network for rows 16k..16k+15 into those cells'
-//      output rows and arrives on named barrier 2; the other warps only
-//      arrive on barrier 1 and go on with their step;
-//   3. a live warp takes its step, waiting on barrier 2 only where cp/R is
-//      first needed (after its rates); a warp without a cell waits on it
-//      directly;
-//   4. every warp reads the iteration's counter: the CTA leaves together when
-//      no warp stays (no cell and, serving, the grid-wide exit reached), and
-//      sleeps while no warp has a cell.
-// Counters rotate over three slots: the evaluator of tile 0 clears the slot
-// of iteration i + 2 after barrier 1 of iteration i, when every reader of
-// that slot (iteration i - 1) has passed and no writer (iteration i + 2) can
-// have started.
+// cell per warp (G = 32) in warps 0 .. net_cells-1, and one evaluator warp
+// (the last) that runs the network on 16-row MMA tiles for the cells:
+//   - a cell warp, at the start of a step whose T is inside the network's
+//     range, publishes its scaled T and then a new request tag in shared
+//     memory, takes the step's rates, and waits for its answer tag only
+//     where cp/R is first needed (the temperature equation);
+//   - the evaluator loops over the tiles; a tile with a fresh request is
+//     evaluated for all its rows (a row without a new request gets the same
+//     values again for its unchanged T), written to the cells' output rows,
+//     and then answered by copying the request tags it read;
+//   - the evaluator leaves when every cell warp has left.
+// Cell warps never wait for one another, and the network's 48 MMAs serve 16
+// cells.  Tags go after the data they cover (fence in between) and are read
+// before it.
 __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = L.S;
   const TablesF tb = stage_tables_mixed(L, smem_raw);
   const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5, nthreads = blockDim.x;
+  const int ncells = L.net_cells;
+  const int rows = (ncells + 15) / 16 * 16;
   const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n);
   const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, true);
   unsigned char* cells = smem_raw + tables;
-  MixedCell cs = mixed_cell(L, cells + (size_t)warp * cell_bytes);
-  const int tiles = (nwarps + 15) / 16;
-  float* sT = reinterpret_cast<float*>(cells + (size_t)nwarps * cell_bytes);
-  __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sT + tiles * 16);
-  int* s_count = reinterpret_cast<int*>(act + tiles * 16 * kNetActLd);
+  float* sT = reinterpret_cast<float*>(cells + (size_t)ncells * cell_bytes);
+  int* tag_req = reinterpret_cast<int*>(sT + rows);
+  int* tag_ans = tag_req + rows;
+  float* t16 = reinterpret_cast<float*>(tag_ans + rows);
+  __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(t16 + 16);
+  int* s_active = reinterpret_cast<int*>(act + 16 * kNetActLd);
   // cell r's output row is at a fixed offset in its cell block: rows cell_bytes apart
   const int out_ld = (int)(cell_bytes / sizeof(float));
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    sT[r] = 0.0f;
+    tag_req[r] = 0;
+    tag_ans[r] = 0;
+  }
+  if (threadIdx.x == 0) *s_active = ncells;
+  __syncthreads();
+
+  if (warp == ncells) {
+    // ---- evaluator
+    float* th0 = mixed_cell(L, cells).Th;
+    while (*(volatile int*)s_active > 0) {
+      bool worked = false;
+      for (int k = 0; k < rows / 16; ++k) {
+        const int r = k * 16 + (l & 15);
+        int req = 0;
+        bool fresh = false;
+        if (l < 16 && r < ncells) {
+          req = *(volatile int*)&tag_req[r];
+          fresh = req != *(volatile int*)&tag_ans[r];
+        }
+        if (!__any_sync(0xffffffffu, fresh)) continue;
+        __threadfence_block();  // the tags before the temperatures they cover
+        if (l < 16) t16[l] = *(volatile float*)&sT[k * 16 + l];
+        __syncwarp();
+        mlp_eval_warp16(L.mlp, t16, act, th0 + (size_t)k * 16 * out_ld, out_ld,
+                        min(16, ncells - k * 16), 0, L.mlp_needed);
+        __threadfence_block();  // the outputs before their answers
+        if (fresh) *(volatile int*)&tag_ans[r] = req;
+        worked = true;
+      }
+      if (!worked) __nanosleep(64);
+    }
+    return;
+  }
+
+  // ---- cell warps
+  MixedCell cs = mixed_cell(L, cells + (size_t)warp * cell_bytes);
   for (int i = l; i < S; i += 32) {
     cs.Y[i] = 0.0;
     cs.Yf[i] = 0.0f;
   }
-  if (threadIdx.x < 3) s_count[threadIdx.x] = 0;
-  if (threadIdx.x < tiles * 16) sT[threadIdx.x] = 0.0f;
-  __syncthreads();
-  const bool evaluator = (warp & 15) == 0;
-  const int tile = warp >> 4;
-
   const unsigned long long n = (unsigned long long)L.n_cells;
   CellState st = idle_cell_state();
   float Pf = (float)kPatm;
@@ -505,13 +558,11 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
   bool idle_committed = false;
   unsigned idle_sleep = 1000u;
   int serve_skip = 0;
-  bool exhausted = false, leaving = false;
-  int slot = 0;  // this iteration's counter (rotates 0, 1, 2)
+  bool exhausted = false;
+  int tag = 0;
   while (true) {
     long long c = -1;
-    if (leaving) {
-      // decided to leave: claims nothing, waits for the rest of the CTA
-    } else if (!L.serve) {
+    if (!L.serve) {
       c = refill<32>(L.counter, n, st.cell < 0, exhausted);
     } else if (serve_skip > 0) {
       --serve_skip;
@@ -522,47 +573,32 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
     }
     if (c >= 0) load_mixed_cell<32>(L, c, l, cs, st, Pf);
     __syncwarp();
-    const bool live = st.cell >= 0;  // warp-uniform
-    if (!live && !leaving) {
-      if (!L.serve) leaving = exhausted;
-      else leaving = serve_idle(L, idle_since, idle_committed);
-    }
-    if (live) idle_since = 0;
-    int* cnt = s_count + slot;
-    if (l == 0) {
-      if (live || !leaving) atomicAdd(cnt, live ? 0x10001 : 1);  // staying (+ live << 16)
-      sT[warp] = live ? ((float)st.T - kTMid) / kTHalf : 0.0f;
-    }
-    __threadfence_block();
-    __syncwarp();
-    if (evaluator) {
-      asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-      if (warp == 0 && l == 0) s_count[slot == 0 ? 2 : slot - 1] = 0;  // slot of iteration + 2
-      mlp_eval_warp16(L.mlp, sT + tile * 16, act + tile * 16 * kNetActLd,
-                      cs.Th, out_ld, min(16, nwarps - tile * 16), 0, L.mlp_needed);
-      __threadfence_block();
-      asm volatile("bar.arrive 2, %0;" ::"r"(nthreads) : "memory");
-    } else {
-      asm volatile("bar.arrive 1, %0;" ::"r"(nthreads) : "memory");
-    }
-    if (live) {
-      idle_sleep = 1000u;
-      const int outcome = step_mixed<32, true>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
-                                               cs.Hist, cs.Rof, Pf, l, st, cs.Th,
-                                               evaluator ? 0 : nthreads);
-      if (outcome >= 0) store_mixed_cell<32>(L, l, cs, st, outcome);
-    } else if (!evaluator) {
-      asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
-    }
-    const int v = *(volatile int*)cnt;  // complete: every warp counted before barrier 1
-    slot = slot == 2 ? 0 : slot + 1;
-    if ((v & 0xFFFF) == 0) break;       // nobody stays: the CTA leaves together
-    if ((v >> 16) == 0 && L.serve) {    // no cell in the CTA: sleep between looks
-      serve_skip = 0;
+    if (st.cell < 0) {
+      if (!L.serve) break;
+      if (serve_idle(L, idle_since, idle_committed)) break;
       __nanosleep(idle_sleep);
       idle_sleep = min(2u * idle_sleep, 32000u);
+      serve_skip = 0;
+      continue;
     }
+    idle_since = 0;
+    idle_sleep = 1000u;
+    if (st.T >= kMlpTLow && st.T <= kMlpTHigh) {
+      ++tag;  // warp-uniform
+      if (l == 0) {
+        *(volatile float*)&sT[warp] = ((float)st.T - kTMid) / kTHalf;
+        __threadfence_block();
+        *(volatile int*)&tag_req[warp] = tag;
+      }
+      __syncwarp();
+    }
+    const int outcome = step_mixed<32, true>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
+                                             cs.Hist, cs.Rof, Pf, l, st, cs.Th,
+                                             tag_ans + warp, tag);
+    if (outcome >= 0) store_mixed_cell<32>(L, l, cs, st, outcome);
   }
+  __syncwarp();
+  if (l == 0) atomicSub(s_active, 1);
 }
 
 }  // namespace stev
