@@ -145,6 +145,32 @@ def barrier(dist):
         dist.barrier()
 
 
+def max_over_ranks(dist, x: float, device=None) -> float:
+    """The slowest rank's value (time-like); x itself with one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float, device=None) -> float:
+    """Every rank's x added (cells processed)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+def whole_job_rate(dist, seconds: float, units: float, device=None) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: each rank its own batch, no data exchange)."""
+    return sum_over_ranks(dist, units, device) / max_over_ranks(dist, seconds, device)
+
+
 def cpu_baseline(mech, T, P, Y, dt, target_s: float = 15.0, **opts):
     """The oracle as it stands on this host's cores, on a bounded sample."""
     import oracle
@@ -498,16 +524,8 @@ def run_ours(args):
     cell_steps = int(it_np.astype(np.int64).sum())
     status = np.bincount(out[3].cpu().numpy(), minlength=4)
 
-    t_max = dev_s
-    total_cells = n * args.steps
-    if dist is not None:
-        t = torch.tensor([dev_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([float(total_cells)], device=dev)
-        dist.all_reduce(c)
-        total_cells = int(c.item())
-    value = total_cells / t_max
+    t_max = max_over_ranks(dist, dev_s, dev)
+    value = whole_job_rate(dist, dev_s, n * args.steps, dev)
 
     # end to end through the host-pointer entry point, pinned host buffers
     e2e = None
@@ -525,11 +543,7 @@ def run_ours(args):
         for _ in range(ke):
             m.solve_host(hT, hP, hY, dt, out=ho)
         el = time.time() - t0
-        if dist is not None:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": n * world * ke / el, "unit": UNIT,
+        e2e = {"value": whole_job_rate(dist, el, n * ke, dev), "unit": UNIT,
                "h2d_bytes_per_step": int(hT.nbytes + hP.nbytes + hY.nbytes),
                "d2h_bytes_per_step": int(sum(x.nbytes for x in ho)), "steps": ke}
     trained_scale = m.mlp_params() if args.thermo == "mlp" else None
@@ -540,13 +554,10 @@ def run_ours(args):
         msx, _, _ = timed_solves(mc, Td, Pd, Yd, dt, out, 1, args.warmup, args.warmup_cells,
                                  stream, dist)
         itx = out[2].cpu().numpy().astype(np.int64)
-        tx = msx[0] / 1e3
-        if dist is not None:
-            t = torch.tensor([tx], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tx = float(t.item())
+        tx = max_over_ranks(dist, msx[0] / 1e3, dev)
         ach = ops * int(itx.sum()) / (msx[0] / 1e3)
-        return {"value": n * world / tx, "unit": UNIT, "ms_per_step": tx * 1e3, "steps": 1,
+        return {"value": whole_job_rate(dist, msx[0] / 1e3, n, dev), "unit": UNIT,
+                "ms_per_step": tx * 1e3, "steps": 1,
                 "warmup": args.warmup, "cell_steps_per_s": int(itx.sum()) / tx,
                 "roofline": {"bound": "alu", "achieved": 2 * ach / 1e12,
                              "peak": 2 * FP64_PEAK_OPS / 1e12, "unit": "TFLOP/s",

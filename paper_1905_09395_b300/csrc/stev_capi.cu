@@ -189,7 +189,7 @@ static stev_status configure(stev_mechanism* m) {
   const size_t limit = prop.sharedMemPerBlockOptin;
   // the network kernel adds an evaluator warp and per-CTA buffers (sized here
   // for its largest CTA)
-  const int max_cells = net ? kMaxBlockMixedNet / 32 - 1 : (mixed ? kMaxBlockMixed : kMaxBlock) / G;
+  const int max_cells = net ? kMaxBlockMixedNet / 32 - 2 : (mixed ? kMaxBlockMixed : kMaxBlock) / G;
   const size_t extra = net ? net_cta_smem_bytes(max_cells) : 0;
   if (tables + extra + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
   int cells = (int)((limit - tables - extra) / cell);
@@ -198,7 +198,7 @@ static stev_status configure(stev_mechanism* m) {
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
   const size_t smem = tables + (size_t)cells * cell + (net ? net_cta_smem_bytes(cells) : 0);
-  const int block = cells * G + (net ? 32 : 0);
+  const int block = cells * G + (net ? 32 * net_evaluators(cells) : 0);
   KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo);
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

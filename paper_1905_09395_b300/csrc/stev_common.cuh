@@ -42,6 +42,7 @@ struct CellState {
   int nhist;
   double lnT;       // mixed kernel: ln T kept up to date incrementally
   double dt;        // this cell's fluid time step t_f
+  double hcap;      // mixed kernel: t_f * delta_max (Eq. 4's time cap)
   long long lc;     // index inside its batch
   int b;            // its batch (batched launches)
 };
@@ -84,6 +85,11 @@ __device__ __forceinline__ CellIO cell_io(const Launch& L, int b) {
   }
   return io;
 }
+
+// Bit pattern of a double as a signed integer: for values >= 0 (and +inf,
+// NaN) the integers order like the values, and a negative value's pattern is
+// negative, so range tests and min / max of such values need no FP64 unit.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;

@@ -33,7 +33,7 @@ constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
 constexpr int kNone = 0xFF;
 constexpr int kMaxBlock = 512;       // threads per CTA of the FP64 persistent kernel
 constexpr int kMaxBlockMixed = 768;  // threads per CTA of the mixed persistent kernel
-constexpr int kMaxBlockMixedNet = 672;  // ... with the thermo network: 20 cell warps + 1 evaluator
+constexpr int kMaxBlockMixedNet = 704;  // ... with the thermo network: 20 cell warps + 2 evaluators
 
 enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
@@ -157,14 +157,16 @@ __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, 
   return (b + 15) & ~(size_t)15;
 }
 
+// The network kernel's evaluator warps: two (each answering half of the
+// CTA's cells, at most 16 rows) unless the CTA holds 8 cells or fewer.
+__host__ __device__ inline int net_evaluators(int cells) { return cells > 8 ? 2 : 1; }
+
 // Per-CTA buffers of the network kernel for `cells` resident cells (one per
-// warp): the published scaled temperatures and request / answer tags (padded
-// to whole 16-row tiles), the evaluator's 16 temperatures and 16 x 72 BF16
-// activation tile, and the count of cell warps still running.
+// warp, at most 32): the published scaled temperatures and request / answer
+// tags, each evaluator's 16 temperatures and 16 x 72 BF16 activation tile, and
+// the count of cell warps still running.
 constexpr int kNetActLd = 64 + 8;
 __host__ __device__ inline size_t net_cta_smem_bytes(int cells) {
-  const int rows = (cells + 15) / 16 * 16;
-  return (size_t)rows * 4 * 3 + 16 * 4 + (size_t)16 * kNetActLd * 2 + 16;
+  return (size_t)32 * 4 * 3 + (size_t)net_evaluators(cells) * (16 * 4 + 16 * kNetActLd * 2) + 16;
 }
-
 }  // namespace stev

@@ -47,6 +47,12 @@ struct TablesF {
   const float* tw;    // float twiddles
 };
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ float lg2f_approx(float x) {
   float r;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -62,15 +68,57 @@ __device__ __forceinline__ double log1p_small(double u) {
   return c * u;
 }
 
+// The thermo network's outputs for a cell (MLP kernels): waits until the
+// evaluator has answered request net_tag (bounded; on a timeout the step
+// takes the polynomials and counts a stall), then adds Y cp/R / W to cpp
+// (and sets H/RT with L.mlp_h).  Returns the group's sum of cpp.
+template <int G>
+__device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, const float* cYf,
+                                            float* cH, const float* cTh,
+                                            const volatile int* net_ans, int net_tag,
+                                            bool use_net, double T, float Tf, float invTf, int l,
+                                            float cpp) {
+  const int S = L.S;
+  if (use_net) {
+    bool answered = *net_ans == net_tag;
+    for (int k = 0; !answered && k < (1 << 18); ++k) {
+      __nanosleep(128);
+      answered = *net_ans == net_tag;
+    }
+    answered = __all_sync(0xffffffffu, answered);
+    __threadfence_block();
+    if (answered) {
+      for (int i = l; i < S; i += G) {
+        cpp = fmaf(cYf[i] * cTh[i], tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+        if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
+      }
+    } else {
+      if (l == 0) atomicAdd(L.net_stalls, 1ULL);
+      for (int i = l; i < S; i += G) {
+        const float* b = tb.spf + i * SPF_STRIDE +
+                         (T < tb.sp[i * SP_STRIDE + SP_TSPLIT] ? SPF_LOW : SPF_HIGH);
+        const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf,
+                                    b[BF_A1]), Tf, b[BF_A0]);
+        cpp = fmaf(cYf[i] * cpR, tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+        if (L.mlp_h) {
+          const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
+          cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+        }
+      }
+    }
+  }
+  return group_sum<G>(cpp);
+}
+
 // MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
 // (Sec. 3) whenever T is inside its training range; outside it, and for G/RT
 // always, the NASA-7 polynomials are used.  The CTA's evaluator warp runs the
 // network for the published temperatures of 16 cells at a time
 // (stev_mixed_net_kernel); this cell's request carries tag net_tag, and its
 // outputs (cp/R, then H/R) are in cTh once *net_ans == net_tag.  The step
-// waits for that only where it first needs them, after the rates, and for at
-// most ~2^20 sleeps; on a timeout it takes the polynomials for this step and
-// counts a stall (never expected).
+// waits for that only where it first needs them: with H/RT from the network,
+// before the production rates; with cp/R only, before the temperature update,
+// after the damper (net_thermo).
 template <int G, bool MLP>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
                                           float* cYf, float2* cG2, float* cC, float* cH,
@@ -81,8 +129,12 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   const double T = st.T;
   const bool use_net = MLP && T >= kMlpTLow && T <= kMlpTHigh;  // one cell per warp
   const double lnT = st.lnT;        // FP64: feeds G/RT
-  const double invT = 1.0 / T;
   const float Tf = (float)T;
+  // 1/T in FP64: the FP32 reciprocal refined by two Newton steps (each squares
+  // the relative error: 2^-22 -> 2^-44 -> below the last bit)
+  double invT = (double)rcp_approx(Tf);
+  invT = fma(invT, fma(-T, invT, 1.0), invT);
+  invT = fma(invT, fma(-T, invT, 1.0), invT);
   const float invTf = 1.0f / Tf;
   const float lg2Tf = lg2f_approx(Tf);
 
@@ -92,7 +144,11 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   const float sumYW = group_sum<G>(part);
   const float rho = Pf / ((float)kRu * Tf * sumYW);
 
-  // thermo: cp/R, H/RT in FP32; G/RT in FP64 (in log2 units, G/RT * log2 e)
+  // thermo: cp/R, H/RT in FP32; G/RT in FP64, in log2 units and with the
+  // standard-state pressure term of Eq. 30 folded in: g2 = (G/RT) log2 e -
+  // lg2(P_atm/RT), so that a reaction's sum of nu g2 is its whole exponent
+  // (sum nu = dN carries the pressure term)
+  const double lg2Pref = (L.ln_patm_over_ru - lnT) * kLog2e;
   float cpp = 0.0f;
   for (int i = l; i < S; i += G) {
     const float* spf = tb.spf + i * SPF_STRIDE;
@@ -111,7 +167,8 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
       cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
     }
     const double gp = fma(fma(fma(bd[B_G4], T, bd[B_G3]), T, bd[B_G2]), T, bd[B_H1]);
-    const double g2 = (fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T) * kLog2e;
+    const double g2 =
+        fma(fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T, kLog2e, -lg2Pref);
     const float ghi = (float)g2;
     cG2[i] = make_float2(ghi, (float)(g2 - (double)ghi));  // g2 == hi + lo to ~2^-48
     const float y = fmaxf(Yi, 0.0f);
@@ -123,10 +180,8 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   __syncwarp();
 
   // rates of progress: kf = 2^(lg2 A + beta lg2 T - Ea/R log2e / T) (FP32);
-  // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e summed exactly
-  const double lg2Pref = (L.ln_patm_over_ru - lnT) * kLog2e;
-  const float prefHi = (float)lg2Pref;
-  const float prefLo = (float)(lg2Pref - (double)prefHi);
+  // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e = sum nu g2, summed
+  // exactly
   const int ktap = st.nhist % N;
   for (int r = l; r < R; r += G) {
     const float4 rx = tb.rxf[r];
@@ -138,8 +193,8 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     if (a1 != kNone) q *= cC[a1];
     float rof = 1.0f;
     if (ri.z) {
-      // x = sum nu g2 - dN lg2Pref as a float pair (s, e): TwoSum on the
-      // high parts, plain sums of the error terms and low parts
+      // x = sum nu g2 as a float pair (s, e): TwoSum on the high parts,
+      // plain sums of the error terms and low parts
       const float2 gp0 = cG2[p0], ga0 = cG2[a0];
       float sx, e, t;
       two_sum(gp0.x, -ga0.x, sx, t);
@@ -154,10 +209,6 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
         two_sum(sx, g.x, sx, t);
         e += t + g.y;
       }
-      if (rx.w != 0.0f) {  // dN in {-1, 1}: exact scaling of the pair
-        two_sum(sx, -rx.w * prefHi, sx, t);
-        e += t - rx.w * prefLo;
-      }
       const float x = sx + e;
       float rev = ex2f(lg2kf + x) * cC[p0];
       if (p1 != kNone) rev *= cC[p1];
@@ -171,37 +222,8 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   }
   __syncwarp();
 
-  if (MLP) {
-    if (use_net) {
-      // the network's outputs for this cell (the evaluator ran meanwhile)
-      bool answered = *net_ans == net_tag;
-      for (int k = 0; !answered && k < (1 << 20); ++k) {
-        __nanosleep(32);
-        answered = *net_ans == net_tag;
-      }
-      answered = __all_sync(0xffffffffu, answered);
-      __threadfence_block();
-      if (answered) {
-        for (int i = l; i < S; i += G) {
-          cpp = fmaf(cYf[i] * cTh[i], tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
-          if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
-        }
-      } else {
-        if (l == 0) atomicAdd(L.net_stalls, 1ULL);
-        for (int i = l; i < S; i += G) {
-          const float* b = tb.spf + i * SPF_STRIDE + (T < tb.sp[i * SP_STRIDE + SP_TSPLIT] ? SPF_LOW : SPF_HIGH);
-          const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf,
-                                      b[BF_A1]), Tf, b[BF_A0]);
-          cpp = fmaf(cYf[i] * cpR, tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
-          if (L.mlp_h) {
-            const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
-            cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
-          }
-        }
-      }
-    }
-    cpsum = group_sum<G>(cpp);
-  }
+  if (MLP && L.mlp_h) cpsum = net_thermo<G>(L, tb, cYf, cH, cTh, net_ans, net_tag, use_net, T, Tf,
+                                              invTf, l, cpp);
 
   // production rates, dY/dt, dT/dt terms and the limiter (FP32)
   const float invRho = 1.0f / rho;
@@ -222,10 +244,13 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   }
   const float hw = group_sum<G>(hwp);
   tmin = group_min<G>(tmin);
-  const float dTdt = -(Tf * hw) / (rho * cpsum);
-  double h = fmin((double)tmin, st.dt * L.delta_max);
-  const bool last = (h >= st.t_rem);
-  if (last) h = st.t_rem;
+  float dTdt = 0.0f;
+  if (!MLP) dTdt = -(Tf * hw) / (rho * cpsum);
+  // h = min(tmin, t_f delta_max), the last step ends at t_f; all >= 0, so the
+  // comparisons run on the bit patterns
+  const long long hb = min(dbits((double)tmin), dbits(st.hcap));
+  const bool last = hb >= dbits(st.t_rem);
+  const double h = last ? st.t_rem : __longlong_as_double(hb);
   const float hf = (float)h;
 
   // ringing detection and damping (Eqs. 8-13), FP32
@@ -273,6 +298,14 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     st.nhist += 1;
   }
 
+  if (MLP) {
+    // cp/R only: its network answer is first needed here, which leaves the
+    // evaluator the rates, the limiter and the damper to answer in
+    if (!L.mlp_h) cpsum = net_thermo<G>(L, tb, cYf, cH, cTh, net_ans, net_tag, use_net, T, Tf,
+                                        invTf, l, cpp);
+    dTdt = -(Tf * hw) / (rho * cpsum);
+  }
+
   // forward Euler in FP64 (Eq. 18)
   bool bad = false;
   for (int i = l; i < S; i += G) {
@@ -288,14 +321,15 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   // series while |u| <= 2^-10; the library log every 256 steps and on larger
   // changes keeps the accumulated rounding below ~1e-13
   const double u = (st.T - T) * invT;
-  if (fabs(u) <= 0x1p-10 && (st.it & 255) != 0)
+  if ((dbits(u) & 0x7FFFFFFFFFFFFFFFLL) <= dbits(0x1p-10) && (st.it & 255) != 0)
     st.lnT = lnT + log1p_small(u);
   else
     st.lnT = log(st.T);
-  bad = group_any<G>(bad) || !isfinite(st.T);
+  const long long Tb = dbits(st.T);
+  bad = group_any<G>(bad) || (Tb & 0x7FF0000000000000LL) == 0x7FF0000000000000LL;
   __syncwarp();
   if (bad) return 2;
-  if (st.T < 200.0 || st.T > 6000.0) return 3;
+  if (Tb < dbits(200.0) || Tb > dbits(6000.0)) return 3;
   if (last) return 0;
   if (st.it >= L.max_iters) return 1;
   return -1;
@@ -356,6 +390,7 @@ __device__ __forceinline__ CellState idle_cell_state() {
   st.P = kPatm;
   st.t_rem = 1.0;
   st.dt = 1.0;
+  st.hcap = 0.01;
   st.lc = 0;
   st.b = 0;
   st.it = 0;
@@ -385,6 +420,7 @@ __device__ __forceinline__ void load_mixed_cell(const Launch& L, long long c, in
   st.T = __ldcg(io.T + lc);  // L1 bypass: serving reuses these addresses
   st.P = __ldcg(io.P + lc);
   st.dt = io.dt;
+  st.hcap = io.dt * L.delta_max;
   st.t_rem = io.dt;
   st.it = 0;
   st.nhist = 0;
@@ -477,17 +513,18 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
 }
 
 // Mixed-precision persistent kernel with the thermo network (Sec. 3): one
-// cell per warp (G = 32) in warps 0 .. net_cells-1, and one evaluator warp
-// (the last) that runs the network on 16-row MMA tiles for the cells:
+// cell per warp (G = 32) in warps 0 .. net_cells-1, and one or two evaluator
+// warps (the last), each running the network on a 16-row MMA tile for its
+// half of the cells:
 //   - a cell warp, at the start of a step whose T is inside the network's
 //     range, publishes its scaled T and then a new request tag in shared
 //     memory, takes the step's rates, and waits for its answer tag only
 //     where cp/R is first needed (the temperature equation);
-//   - the evaluator loops over the tiles; a tile with a fresh request is
-//     evaluated for all its rows (a row without a new request gets the same
-//     values again for its unchanged T), written to the cells' output rows,
-//     and then answered by copying the request tags it read;
-//   - the evaluator leaves when every cell warp has left.
+//   - an evaluator polls its rows; once 3/4 of them have fresh requests, or
+//     the oldest has waited 4 us, it evaluates all of them (a row without a
+//     new request gets the same values again for its unchanged T), writes the
+//     cells' output rows, and answers by copying the request tags it read;
+//   - the evaluators leave when every cell warp has left.
 // Cell warps never wait for one another, and the network's 48 MMAs serve 16
 // cells.  Tags go after the data they cover (fence in between) and are read
 // before it.
@@ -496,20 +533,21 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
   const int S = L.S;
   const TablesF tb = stage_tables_mixed(L, smem_raw);
   const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int ncells = L.net_cells;
-  const int rows = (ncells + 15) / 16 * 16;
+  const int ncells = L.net_cells;  // <= 32
+  const int nev = net_evaluators(ncells);
+  const int per_ev = (ncells + nev - 1) / nev;  // rows each evaluator answers, <= 16
   const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n);
   const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, true);
   unsigned char* cells = smem_raw + tables;
   float* sT = reinterpret_cast<float*>(cells + (size_t)ncells * cell_bytes);
-  int* tag_req = reinterpret_cast<int*>(sT + rows);
-  int* tag_ans = tag_req + rows;
-  float* t16 = reinterpret_cast<float*>(tag_ans + rows);
-  __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(t16 + 16);
-  int* s_active = reinterpret_cast<int*>(act + 16 * kNetActLd);
+  int* tag_req = reinterpret_cast<int*>(sT + 32);
+  int* tag_ans = tag_req + 32;
+  float* ev_base = reinterpret_cast<float*>(tag_ans + 32);
+  constexpr int kEvFloats = 16 + 16 * kNetActLd / 2;  // 16 temperatures + the BF16 tile
+  int* s_active = reinterpret_cast<int*>(ev_base + nev * kEvFloats);
   // cell r's output row is at a fixed offset in its cell block: rows cell_bytes apart
   const int out_ld = (int)(cell_bytes / sizeof(float));
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+  for (int r = threadIdx.x; r < 32; r += blockDim.x) {
     sT[r] = 0.0f;
     tag_req[r] = 0;
     tag_ans[r] = 0;
@@ -517,30 +555,44 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
   if (threadIdx.x == 0) *s_active = ncells;
   __syncthreads();
 
-  if (warp == ncells) {
-    // ---- evaluator
-    float* th0 = mixed_cell(L, cells).Th;
+  if (warp >= ncells) {
+    // ---- evaluator e: rows r0 .. r0 + nrow - 1
+    const int e = warp - ncells;
+    const int r0 = e * per_ev, nrow = min(per_ev, ncells - r0);
+    float* t16 = ev_base + e * kEvFloats;
+    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(t16 + 16);
+    float* th0 = mixed_cell(L, cells + (size_t)r0 * cell_bytes).Th;
+    const int r = r0 + (l & 15);
+    const bool mine = l < 16 && l < nrow;
+    unsigned long long first = 0;  // when the oldest unanswered request was seen
     while (*(volatile int*)s_active > 0) {
-      bool worked = false;
-      for (int k = 0; k < rows / 16; ++k) {
-        const int r = k * 16 + (l & 15);
-        int req = 0;
-        bool fresh = false;
-        if (l < 16 && r < ncells) {
-          req = *(volatile int*)&tag_req[r];
-          fresh = req != *(volatile int*)&tag_ans[r];
-        }
-        if (!__any_sync(0xffffffffu, fresh)) continue;
-        __threadfence_block();  // the tags before the temperatures they cover
-        if (l < 16) t16[l] = *(volatile float*)&sT[k * 16 + l];
-        __syncwarp();
-        mlp_eval_warp16(L.mlp, t16, act, th0 + (size_t)k * 16 * out_ld, out_ld,
-                        min(16, ncells - k * 16), 0, L.mlp_needed);
-        __threadfence_block();  // the outputs before their answers
-        if (fresh) *(volatile int*)&tag_ans[r] = req;
-        worked = true;
+      int req = 0;
+      bool fresh = false;
+      if (mine) {
+        req = *(volatile int*)&tag_req[r];
+        fresh = req != *(volatile int*)&tag_ans[r];
       }
-      if (!worked) __nanosleep(64);
+      const int nfresh = __popc(__ballot_sync(0xffffffffu, fresh));
+      if (nfresh == 0) {
+        first = 0;
+        __nanosleep(128);
+        continue;
+      }
+      // batch: wait for 3/4 of the rows or until the oldest request is 4 us
+      // old (cells ask at the start of a step and need the answer near its end)
+      const unsigned long long now = __shfl_sync(0xffffffffu, gtimer_ns(), 0);
+      if (first == 0) first = now;
+      if (4 * nfresh < 3 * nrow && now - first < 4000) {
+        __nanosleep(256);
+        continue;
+      }
+      first = 0;
+      __threadfence_block();  // the tags before the temperatures they cover
+      if (l < 16) t16[l] = mine ? *(volatile float*)&sT[r] : 0.0f;
+      __syncwarp();
+      mlp_eval_warp16(L.mlp, t16, act, th0, out_ld, nrow, 0, L.mlp_needed);
+      __threadfence_block();  // the outputs before their answers
+      if (fresh) *(volatile int*)&tag_ans[r] = req;
     }
     return;
   }
