@@ -171,23 +171,41 @@ def whole_job_rate(dist, seconds: float, units: float, device=None) -> float:
     return sum_over_ranks(dist, units, device) / max_over_ranks(dist, seconds, device)
 
 
-def cpu_baseline(mech, T, P, Y, dt, target_s: float = 15.0, **opts):
-    """The oracle as it stands on this host's cores, on a bounded sample."""
+def cpu_baseline(mech, T, P, Y, dt, target_s: float = 15.0, keep=None, **opts):
+    """The oracle as it stands on this host's cores, on a bounded sample.
+    keep (a dict) receives the oracle's results on the sample cells."""
     import oracle
     cores = os.cpu_count() or 1
     n = max(cores, 8)
     t0 = time.time()
-    oracle.solve(mech, T[:n], P[:n], Y[:n], dt, n_threads=cores, **opts)
+    res = oracle.solve(mech, T[:n], P[:n], Y[:n], dt, n_threads=cores, **opts)
     first = time.time() - t0
     # grow the sample to ~target_s of work (cells are independent and alike)
     n2 = int(min(len(T), max(n, n * target_s / max(first, 1e-3))))
     if n2 > n:
         t0 = time.time()
-        oracle.solve(mech, T[:n2], P[:n2], Y[:n2], dt, n_threads=cores, **opts)
+        res = oracle.solve(mech, T[:n2], P[:n2], Y[:n2], dt, n_threads=cores, **opts)
         first = time.time() - t0
         n = n2
+    if keep is not None:
+        keep["ref"] = res
     return {"value": n / first, "unit": UNIT, "cores": min(cores, n), "kind": "oracle",
             "sample": "first %d cells of the same workload, %.1f s" % (n, first)}
+
+
+def oracle_error(gpu, ref, tol_Y, tol_T):
+    """Error of GPU results against the oracle on the same cells.  STEV's final
+    state is ill-conditioned on cells ringing at their limiter's amplitude (a
+    rounding-size change moves them by up to ~2 Y_step^max), so the fraction
+    within the target and the median say more than the maximum."""
+    n = min(len(gpu[0]), len(ref[0]))
+    dY = np.abs(gpu[1][:n] - ref[1][:n]).max(axis=1)
+    dT = np.abs(gpu[0][:n] - ref[0][:n])
+    return {"cells": int(n), "target": {"max_dY": tol_Y, "dT_K": tol_T},
+            "within_target": float(np.mean((dY <= tol_Y) & (dT <= tol_T))),
+            "median_dY": float(np.median(dY)), "max_dY": float(dY.max()),
+            "median_dT_K": float(np.median(dT)), "max_dT_K": float(dT.max()),
+            "status_equal": float(np.mean(gpu[3][:n] == ref[3][:n]))}
 
 
 def run_reference(args):
@@ -523,6 +541,7 @@ def run_ours(args):
     it_np = out[2].cpu().numpy()
     cell_steps = int(it_np.astype(np.int64).sum())
     status = np.bincount(out[3].cpu().numpy(), minlength=4)
+    head = [x[:4096].cpu().numpy() for x in out]   # compared with the oracle below
 
     t_max = max_over_ranks(dist, dev_s, dev)
     value = whole_job_rate(dist, dev_s, n * args.steps, dev)
@@ -574,6 +593,7 @@ def run_ours(args):
     if args.precision == "mixed" and not args.no_fp64_compare:
         mf = Mechanism(mech, precision=binding.FP64, **extra)
         plain = one_solve(mf, fp64_ops_per_cell_step(S, R, Rrev, nnz))
+        plain_head = [x[:4096].cpu().numpy() for x in out]
         mf.close()
 
     if rank != 0:
@@ -633,7 +653,13 @@ def run_ours(args):
                                                                  args.serve_seconds,
                                                                  args.serve_drain))
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, **extra)
+        keep = {}
+        line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, keep=keep, **extra)
+        fp64 = args.precision == "fp64"
+        line["oracle_error"] = oracle_error(head, keep["ref"], 1e-8 if fp64 else 1e-4,
+                                            1e-6 if fp64 else 0.5)
+        if plain is not None:
+            plain["oracle_error"] = oracle_error(plain_head, keep["ref"], 1e-8, 1e-6)
     print(json.dumps(line))
     return 0
 

@@ -201,6 +201,32 @@ stev_status stev_mlp_train(stev_mechanism *mech, const double *T_samples, long n
                            int epochs, int batch, float lr, unsigned long long seed,
                            float *loss_per_epoch);
 
+/* Trains the network with Levenberg-Marquardt, the optimizer Sec. 3 uses:
+ * each iteration takes the next `batch` samples (consecutive windows of the
+ * HOST sample array), forms the Jacobian J of the batch's standardised
+ * outputs with respect to every parameter (the library's kernel, FP32) and
+ * the residuals r, then J^T J and J^T r (cuBLAS, FP32), and solves
+ * (J^T J + lambda diag(J^T J) + 1e-12 I) d = J^T r by Cholesky (cuSOLVER,
+ * FP64).  The step p - d is kept if it lowers the batch's mean squared error
+ * (then lambda /= 3), else lambda *= 2 and the solve is repeated, at most 8
+ * times (lambda *= 4 when the matrix is not positive definite).  init: 0 =
+ * Xavier-uniform weights from splitmix64(seed) and fresh output statistics;
+ * 1 = continue from the current network and its statistics (e.g. after
+ * stev_mlp_train).  lambda0 > 0: the starting damping.  loss_per_iter
+ * (HOST, nullable) receives each iteration's batch loss after its step, in
+ * standardised units.  The Jacobian takes batch * 3S * n_params * 4 bytes of
+ * device memory (at most 8 GB).  Synchronous. */
+stev_status stev_mlp_train_lm(stev_mechanism *mech, const double *T_samples, long n_samples,
+                              int iterations, int batch, double lambda0, int init,
+                              unsigned long long seed, float *loss_per_iter);
+
+/* The Jacobian the Levenberg-Marquardt trainer forms: d(standardised output o
+ * at sample s) / d(parameter p) for parameters `params` (HOST) at n <= 4096
+ * HOST temperatures; J (HOST) receives [n * 3S][n_params], row s * 3S + o.
+ * Synchronous. */
+stev_status stev_mlp_jacobian(stev_mechanism *mech, const float *params, const double *T,
+                              long n, float *J);
+
 /* Sets / reads the network parameters (HOST arrays) and the per-output mean and
  * standard deviation ([3S] each) used to undo the standardisation. */
 stev_status stev_mlp_set_params(stev_mechanism *mech, const float *params, long n_params,

@@ -31,6 +31,7 @@ EXPORTS = (
     "stev_mlp_loss_grad", "stev_mlp_eval", "stev_solve_batched",
     "stev_server_create", "stev_server_submit", "stev_server_poll", "stev_server_get_stats",
     "stev_server_clock", "stev_server_stop", "stev_server_destroy", "stev_mlp_stalls",
+    "stev_mlp_train_lm", "stev_mlp_jacobian",
 )
 
 
@@ -100,6 +101,10 @@ def lib():
         L.stev_mlp_num_params.restype = LNG
         L.stev_mlp_train.argtypes = [P, P, LNG, I, I, ctypes.c_float, ctypes.c_ulonglong, P]
         L.stev_mlp_train.restype = I
+        L.stev_mlp_train_lm.argtypes = [P, P, LNG, I, I, D, I, ctypes.c_ulonglong, P]
+        L.stev_mlp_train_lm.restype = I
+        L.stev_mlp_jacobian.argtypes = [P, P, P, LNG, P]
+        L.stev_mlp_jacobian.restype = I
         L.stev_mlp_set_params.argtypes = [P, P, LNG, P, P]
         L.stev_mlp_set_params.restype = I
         L.stev_mlp_get_params.argtypes = [P, P, LNG, P, P]
@@ -294,6 +299,25 @@ class Mechanism:
         _check(lib().stev_mlp_train(self._h, T.ctypes.data, len(T), int(epochs), int(batch),
                                     float(lr), int(seed), hist.ctypes.data))
         return hist
+
+    def mlp_train_lm(self, T_samples, iterations: int = 50, batch: int = 512,
+                     lambda0: float = 1e-2, init: int = 0, seed: int = 0):
+        """Levenberg-Marquardt training (stev_mlp_train_lm); returns the loss of
+        every iteration."""
+        T = _np(T_samples, np.float64)
+        hist = np.zeros(iterations, np.float32)
+        _check(lib().stev_mlp_train_lm(self._h, T.ctypes.data, len(T), int(iterations),
+                                       int(batch), float(lambda0), int(init), int(seed),
+                                       hist.ctypes.data))
+        return hist
+
+    def mlp_jacobian(self, params, T):
+        """d(standardised outputs)/d(params) at host temperatures: [n*3S][n_params]."""
+        p, Tn = _np(params, np.float32), _np(T, np.float64)
+        J = np.zeros((len(Tn) * 3 * self.S, len(p)), np.float32)
+        _check(lib().stev_mlp_jacobian(self._h, p.ctypes.data, Tn.ctypes.data, len(Tn),
+                                       J.ctypes.data))
+        return J
 
     def mlp_params(self):
         """(flat float32 parameters, mean [3S], std [3S])."""

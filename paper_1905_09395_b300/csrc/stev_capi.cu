@@ -10,7 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
 
 #include "../../include/stev.h"
 #include "stev_device.cuh"
@@ -458,6 +460,13 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   L.tol_freq = m->opt.tol_freq;
   L.r_fac = m->opt.r_fac;
   L.rof_min = m->opt.rof_min;
+  L.y_step_max_f = (float)m->opt.y_step_max;
+  L.alpha_f = (float)m->opt.alpha;
+  L.tol_ring_f = (float)m->opt.tol_ring;
+  L.tol_freq_f = (float)m->opt.tol_freq;
+  L.r_fac_f = (float)m->opt.r_fac;
+  L.inv_r_fac_f = 1.0f / (float)m->opt.r_fac;
+  L.rof_min_f = (float)m->opt.rof_min;
   L.ln_patm_over_ru = std::log(kPatm / kRu);
   L.n_cells = n;
   L.dt = dt;
@@ -908,6 +917,58 @@ extern "C" stev_status stev_mlp_loss_grad(stev_mechanism* m, const float* params
   return st;
 }
 
+// Training targets at n DEVICE temperatures: the NASA-7 polynomials (FP64,
+// stored FP32) standardised per output.  fresh: compute each output's mean and
+// standard deviation (per-block partial sums added in a fixed order);
+// otherwise mean / stdv are inputs (continuing a trained network).
+static stev_status mlp_make_targets(stev_mechanism* m, const double* dT, long long n,
+                                    float* dtarget, std::vector<float>& mean,
+                                    std::vector<float>& stdv, bool fresh) {
+  const int no = m->mlp_out;
+  const long long tot = n * m->S;
+  mlp_targets_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(m->d_sp, m->S, dT, n, dtarget);
+  CUDA_TRY(cudaGetLastError());
+  if (fresh) {
+    const int mom_blocks = 64;
+    double* dsum = nullptr;
+    CUDA_TRY(cudaMalloc(&dsum, (size_t)2 * no * mom_blocks * 8));
+    mlp_moments_kernel<<<dim3(mom_blocks, no), 256>>>(dtarget, n, no, dsum);
+    std::vector<double> parts((size_t)2 * no * mom_blocks);
+    const cudaError_t e = cudaMemcpy(parts.data(), dsum, parts.size() * 8, cudaMemcpyDeviceToHost);
+    cudaFree(dsum);
+    CUDA_TRY(e);
+    mean.assign(no, 0.0f);
+    stdv.assign(no, 1.0f);
+    for (int c = 0; c < no; ++c) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int b = 0; b < mom_blocks; ++b) {
+        s1 += parts[((size_t)c * mom_blocks + b) * 2];
+        s2 += parts[((size_t)c * mom_blocks + b) * 2 + 1];
+      }
+      const double mu = s1 / n;
+      const double var = std::max(s2 / n - mu * mu, 0.0);
+      mean[c] = (float)mu;
+      stdv[c] = (float)std::max(std::sqrt(var), 1e-6 * std::max(1.0, std::fabs(mu)));
+    }
+  }
+  std::vector<float> stat((size_t)2 * no);
+  for (int c = 0; c < no; ++c) {
+    stat[c] = mean[c];
+    stat[no + c] = 1.0f / stdv[c];
+  }
+  float* dstat = nullptr;
+  CUDA_TRY(cudaMalloc(&dstat, stat.size() * 4));
+  cudaError_t e = cudaMemcpy(dstat, stat.data(), stat.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    mlp_standardise_kernel<<<(unsigned)((n * no + 255) / 256), 256>>>(dtarget, n, no, dstat,
+                                                                       dstat + no);
+    e = cudaDeviceSynchronize();
+  }
+  cudaFree(dstat);
+  CUDA_TRY(e);
+  return STEV_OK;
+}
+
 static inline uint64_t splitmix64(uint64_t& x) {
   uint64_t z = (x += 0x9e3779b97f4a7c15ull);
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -927,12 +988,11 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   if (st != STEV_OK) return st;
   const int no = m->mlp_out, np = m->mlp_np;
   const int mb_tiles = (int)((std::min((long long)batch, (long long)n) + kMlpTile - 1) / kMlpTile);
-  const int mom_blocks = 64;
-  double *dT = nullptr, *dsum = nullptr, *dloss = nullptr, *dlp = nullptr;
-  float *dtarget = nullptr, *dpart = nullptr, *dm1 = nullptr, *dm2 = nullptr, *dstat = nullptr;
+  double *dT = nullptr, *dloss = nullptr, *dlp = nullptr;
+  float *dtarget = nullptr, *dpart = nullptr, *dm1 = nullptr, *dm2 = nullptr;
   auto cleanup = [&]() {
-    cudaFree(dT); cudaFree(dsum); cudaFree(dloss); cudaFree(dtarget); cudaFree(dpart);
-    cudaFree(dm1); cudaFree(dm2); cudaFree(dstat); cudaFree(dlp);
+    cudaFree(dT); cudaFree(dloss); cudaFree(dtarget); cudaFree(dpart);
+    cudaFree(dm1); cudaFree(dm2); cudaFree(dlp);
   };
 #define TRY_CLEAN(expr)                                                                     \
   do {                                                                                      \
@@ -945,8 +1005,6 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   } while (0)
   TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
   TRY_CLEAN(cudaMalloc(&dtarget, (size_t)n * no * 4));
-  TRY_CLEAN(cudaMalloc(&dsum, (size_t)2 * no * mom_blocks * 8));
-  TRY_CLEAN(cudaMalloc(&dstat, (size_t)2 * no * 4));
   TRY_CLEAN(cudaMalloc(&dpart, (size_t)mb_tiles * np * 4));
   TRY_CLEAN(cudaMalloc(&dlp, (size_t)mb_tiles * 8));
   TRY_CLEAN(cudaMalloc(&dm1, (size_t)np * 4));
@@ -954,35 +1012,9 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   TRY_CLEAN(cudaMalloc(&dloss, 8));
   TRY_CLEAN(cudaMemcpy(dT, T_samples, (size_t)n * 8, cudaMemcpyHostToDevice));
   // targets: the polynomials in FP64, standardised per output column
-  {
-    const long long tot = (long long)n * m->S;
-    mlp_targets_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(m->d_sp, m->S, dT, n, dtarget);
-    TRY_CLEAN(cudaGetLastError());
-    mlp_moments_kernel<<<dim3(mom_blocks, no), 256>>>(dtarget, n, no, dsum);
-    TRY_CLEAN(cudaGetLastError());
-  }
-  std::vector<double> parts((size_t)2 * no * mom_blocks);
-  TRY_CLEAN(cudaMemcpy(parts.data(), dsum, parts.size() * 8, cudaMemcpyDeviceToHost));
-  std::vector<float> mean(no), stdv(no), inv(no);
-  for (int c = 0; c < no; ++c) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < mom_blocks; ++b) {
-      s1 += parts[((size_t)c * mom_blocks + b) * 2];
-      s2 += parts[((size_t)c * mom_blocks + b) * 2 + 1];
-    }
-    const double mu = s1 / n;
-    const double var = std::max(s2 / n - mu * mu, 0.0);
-    mean[c] = (float)mu;
-    stdv[c] = (float)std::max(std::sqrt(var), 1e-6 * std::max(1.0, std::fabs(mu)));
-    inv[c] = 1.0f / stdv[c];
-  }
-  TRY_CLEAN(cudaMemcpy(dstat, mean.data(), no * 4, cudaMemcpyHostToDevice));
-  TRY_CLEAN(cudaMemcpy(dstat + no, inv.data(), no * 4, cudaMemcpyHostToDevice));
-  {
-    const long long tot = (long long)n * no;
-    mlp_standardise_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(dtarget, n, no, dstat, dstat + no);
-    TRY_CLEAN(cudaGetLastError());
-  }
+  std::vector<float> mean, stdv;
+  st = mlp_make_targets(m, dT, n, dtarget, mean, stdv, true);
+  if (st != STEV_OK) { cleanup(); return st; }
   // Xavier-uniform initialisation from splitmix64(seed), zero biases
   const MlpOffsets o = mlp_offsets(no);
   std::vector<float> P(np, 0.0f);
@@ -1023,6 +1055,192 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   }
   TRY_CLEAN(cudaMemcpy(P.data(), m->d_mlp_params, (size_t)np * 4, cudaMemcpyDeviceToHost));
 #undef TRY_CLEAN
+  cleanup();
+  return mlp_pack(m, P, mean, stdv);
+}
+
+// --------------------------------------- Levenberg-Marquardt training
+extern "C" stev_status stev_mlp_jacobian(stev_mechanism* m, const float* params, const double* T,
+                                         long n, float* J) {
+  g_err.clear();
+  if (!m || !params || !T || !J) return fail(STEV_EINVAL, "NULL argument");
+  if (n < 1 || n > 4096) return fail(STEV_EINVAL, "n must be in [1, 4096]");
+  const int no = 3 * m->S, np = mlp_n_params(no);
+  float *dp = nullptr, *dJ = nullptr, *dtg = nullptr, *dr = nullptr;
+  double* dT = nullptr;
+  auto cleanup = [&]() { cudaFree(dp); cudaFree(dJ); cudaFree(dtg); cudaFree(dr); cudaFree(dT); };
+#define TRY_CLEAN(expr)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cleanup();                                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? STEV_ENOMEM : STEV_ECUDA, "%s: %s",     \
+                  #expr, cudaGetErrorString(e_));                                           \
+    }                                                                                       \
+  } while (0)
+  TRY_CLEAN(cudaMalloc(&dp, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dJ, (size_t)n * no * np * 4));
+  TRY_CLEAN(cudaMalloc(&dtg, (size_t)n * no * 4));
+  TRY_CLEAN(cudaMalloc(&dr, (size_t)n * no * 4));
+  TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
+  TRY_CLEAN(cudaMemcpy(dp, params, (size_t)np * 4, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemcpy(dT, T, (size_t)n * 8, cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemset(dtg, 0, (size_t)n * no * 4));
+  mlp_jacobian_kernel<<<(unsigned)n, kHid>>>(dp, no, dT, dtg, dJ, dr);
+  TRY_CLEAN(cudaGetLastError());
+  TRY_CLEAN(cudaMemcpy(J, dJ, (size_t)n * no * np * 4, cudaMemcpyDeviceToHost));
+#undef TRY_CLEAN
+  cleanup();
+  return STEV_OK;
+}
+
+extern "C" stev_status stev_mlp_train_lm(stev_mechanism* m, const double* T_samples, long n,
+                                         int iterations, int batch, double lambda0, int init,
+                                         unsigned long long seed, float* loss_per_iter) {
+  g_err.clear();
+  if (!m || !T_samples) return fail(STEV_EINVAL, "NULL argument");
+  if (n < 1 || iterations < 1 || batch < 1 || !(lambda0 > 0.0) || !std::isfinite(lambda0))
+    return fail(STEV_EINVAL, "bad training sizes");
+  if (init != 0 && init != 1) return fail(STEV_EINVAL, "init must be 0 or 1");
+  if (init == 1 && !m->mlp_ready) return fail(STEV_EINVAL, "init = 1 needs a trained network");
+  for (long k = 0; k < n; ++k)
+    if (!(T_samples[k] > 0.0) || !std::isfinite(T_samples[k])) return fail(STEV_EINVAL, "T_samples[%ld] invalid", k);
+  stev_status st = mlp_ensure(m);
+  if (st != STEV_OK) return st;
+  const int no = m->mlp_out, np = m->mlp_np;
+  const long long nb = std::min((long long)batch, (long long)n);
+  const long long rows = nb * no;
+  if ((double)rows * np * 4 > 8e9) return fail(STEV_EINVAL, "batch too large (Jacobian over 8 GB)");
+  double *dT = nullptr, *dAd = nullptr, *dg = nullptr, *dse = nullptr, *dwork = nullptr;
+  float *dtarget = nullptr, *dJ = nullptr, *dr = nullptr, *dA = nullptr, *dgf = nullptr;
+  float *dp = nullptr, *dpn = nullptr;
+  int* dinfo = nullptr;
+  cublasHandle_t cb = nullptr;
+  cusolverDnHandle_t cs = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dT); cudaFree(dAd); cudaFree(dg); cudaFree(dse); cudaFree(dwork); cudaFree(dtarget);
+    cudaFree(dJ); cudaFree(dr); cudaFree(dA); cudaFree(dgf); cudaFree(dp); cudaFree(dpn);
+    cudaFree(dinfo);
+    if (cb) cublasDestroy(cb);
+    if (cs) cusolverDnDestroy(cs);
+  };
+#define TRY_CLEAN(expr)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cleanup();                                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? STEV_ENOMEM : STEV_ECUDA, "%s: %s",     \
+                  #expr, cudaGetErrorString(e_));                                           \
+    }                                                                                       \
+  } while (0)
+#define LIB_CLEAN(expr, what)                                                               \
+  do {                                                                                      \
+    if ((expr) != 0) {                                                                      \
+      cleanup();                                                                            \
+      return fail(STEV_ECUDA, "%s failed", what);                                           \
+    }                                                                                       \
+  } while (0)
+  TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
+  TRY_CLEAN(cudaMalloc(&dtarget, (size_t)n * no * 4));
+  TRY_CLEAN(cudaMalloc(&dJ, (size_t)rows * np * 4));
+  TRY_CLEAN(cudaMalloc(&dr, (size_t)rows * 4));
+  TRY_CLEAN(cudaMalloc(&dA, (size_t)np * np * 4));
+  TRY_CLEAN(cudaMalloc(&dAd, (size_t)np * np * 8));
+  TRY_CLEAN(cudaMalloc(&dgf, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dg, (size_t)np * 8));
+  TRY_CLEAN(cudaMalloc(&dse, (size_t)nb * 8));
+  TRY_CLEAN(cudaMalloc(&dp, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dpn, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dinfo, sizeof(int)));
+  LIB_CLEAN(cublasCreate(&cb), "cublasCreate");
+  LIB_CLEAN(cublasSetMathMode(cb, CUBLAS_PEDANTIC_MATH), "cublasSetMathMode");  // FP32, no TF32
+  LIB_CLEAN(cusolverDnCreate(&cs), "cusolverDnCreate");
+  int lwork = 0;
+  LIB_CLEAN(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, np, dAd, np, &lwork),
+            "cusolverDnDpotrf_bufferSize");
+  TRY_CLEAN(cudaMalloc(&dwork, (size_t)std::max(lwork, 1) * 8));
+  TRY_CLEAN(cudaMemcpy(dT, T_samples, (size_t)n * 8, cudaMemcpyHostToDevice));
+
+  // targets (statistics kept when continuing) and starting parameters
+  std::vector<float> P(np, 0.0f), mean, stdv;
+  if (init == 1) {
+    mean.resize(no);
+    stdv.resize(no);
+    st = stev_mlp_get_params(m, P.data(), np, mean.data(), stdv.data());
+    if (st != STEV_OK) { cleanup(); return st; }
+  }
+  st = mlp_make_targets(m, dT, n, dtarget, mean, stdv, init == 0);
+  if (st != STEV_OK) { cleanup(); return st; }
+  if (init == 0) {
+    const MlpOffsets o = mlp_offsets(no);
+    uint64_t rs = seed;
+    auto uni = [&](float a) { return (float)(((splitmix64(rs) >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0) * a; };
+    for (int k = 0; k < kHid; ++k) P[o.W1 + k] = uni(std::sqrt(6.0f / (1 + kHid)));
+    for (int k = 0; k < kHid * kHid; ++k) P[o.W2 + k] = uni(std::sqrt(6.0f / (kHid + kHid)));
+    for (int k = 0; k < no * kHid; ++k) P[o.W3 + k] = uni(std::sqrt(6.0f / (kHid + no)));
+  }
+  TRY_CLEAN(cudaMemcpy(dp, P.data(), (size_t)np * 4, cudaMemcpyHostToDevice));
+
+  // the batch's mean squared error with parameters p (per-sample sums in order)
+  std::vector<double> se(nb);
+  auto batch_loss = [&](const float* p, long long s0, double* out) -> bool {
+    mlp_sqerr_kernel<<<(unsigned)((nb + 127) / 128), 128>>>(p, no, dT + s0, dtarget + s0 * no, nb, dse);
+    if (cudaMemcpy(se.data(), dse, (size_t)nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    double t = 0.0;
+    for (long long k = 0; k < nb; ++k) t += se[k];
+    *out = t / (double)rows;
+    return true;
+  };
+  double lambda = lambda0;
+  const float one = 1.0f, zero = 0.0f;
+  for (int it = 0; it < iterations; ++it) {
+    const long long s0 = ((long long)it * nb) % std::max(1LL, (long long)n - nb + 1);
+    mlp_jacobian_kernel<<<(unsigned)nb, kHid>>>(dp, no, dT + s0, dtarget + s0 * no, dJ, dr);
+    TRY_CLEAN(cudaGetLastError());
+    // J is row-major [rows][np], i.e. column-major np x rows: A = J^T J, g = J^T r
+    LIB_CLEAN(cublasSsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, np, (int)rows, &one, dJ, np,
+                          &zero, dA, np), "cublasSsyrk");
+    LIB_CLEAN(cublasSgemv(cb, CUBLAS_OP_N, np, (int)rows, &one, dJ, np, dr, 1, &zero, dgf, 1),
+              "cublasSgemv");
+    double loss0 = 0.0, loss1 = 0.0;
+    if (!batch_loss(dp, s0, &loss0)) { cleanup(); return fail(STEV_ECUDA, "loss copy failed"); }
+    bool accepted = false;
+    for (int attempt = 0; attempt < 8 && !accepted; ++attempt) {
+      const long long tot = (long long)np * np;
+      mlp_damp_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(dA, np, lambda, 1e-12, dAd);
+      TRY_CLEAN(cudaGetLastError());
+      LIB_CLEAN(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, np, dAd, np, dwork, lwork, dinfo),
+                "cusolverDnDpotrf");
+      int info = 0;
+      TRY_CLEAN(cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
+      if (info != 0) {  // not positive definite at this damping
+        lambda *= 4.0;
+        continue;
+      }
+      // g (FP64) = J^T r; solve (A + lambda diag A) d = g; p_new = p - d
+      std::vector<float> gf(np);
+      std::vector<double> gd(np);
+      TRY_CLEAN(cudaMemcpy(gf.data(), dgf, (size_t)np * 4, cudaMemcpyDeviceToHost));
+      for (int k = 0; k < np; ++k) gd[k] = gf[k];
+      TRY_CLEAN(cudaMemcpy(dg, gd.data(), (size_t)np * 8, cudaMemcpyHostToDevice));
+      LIB_CLEAN(cusolverDnDpotrs(cs, CUBLAS_FILL_MODE_LOWER, np, 1, dAd, np, dg, np, dinfo),
+                "cusolverDnDpotrs");
+      mlp_step_kernel<<<(np + 255) / 256, 256>>>(dp, dg, np, dpn);
+      TRY_CLEAN(cudaGetLastError());
+      if (!batch_loss(dpn, s0, &loss1)) { cleanup(); return fail(STEV_ECUDA, "loss copy failed"); }
+      if (std::isfinite(loss1) && loss1 < loss0) {
+        std::swap(dp, dpn);
+        lambda = std::max(lambda / 3.0, 1e-9);
+        accepted = true;
+      } else {
+        lambda *= 2.0;
+      }
+    }
+    if (loss_per_iter) loss_per_iter[it] = (float)(accepted ? loss1 : loss0);
+  }
+  TRY_CLEAN(cudaMemcpy(P.data(), dp, (size_t)np * 4, cudaMemcpyDeviceToHost));
+#undef TRY_CLEAN
+#undef LIB_CLEAN
   cleanup();
   return mlp_pack(m, P, mean, stdv);
 }

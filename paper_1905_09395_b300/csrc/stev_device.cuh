@@ -114,6 +114,8 @@ struct Launch {
   int serve_q;
   long long idle_ns;      // the kernel leaves once every warp has been idle this long
   int serve_warps;        // warps in the grid
+  // the options in FP32 for the mixed kernels (converted once, not per use)
+  float y_step_max_f, alpha_f, tol_ring_f, tol_freq_f, r_fac_f, inv_r_fac_f, rof_min_f;
   MlpInfer mlp;           // thermo network (mixed kernel, thermo = MLP)
   int mlp_needed;         // network outputs the solver reads (cp/R [, H/R]), rounded up to 8
   int mlp_h;              // 1: H/RT from the network as well
@@ -162,11 +164,11 @@ __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, 
 __host__ __device__ inline int net_evaluators(int cells) { return cells > 8 ? 2 : 1; }
 
 // Per-CTA buffers of the network kernel for `cells` resident cells (one per
-// warp, at most 32): the published scaled temperatures and request / answer
-// tags, each evaluator's 16 temperatures and 16 x 72 BF16 activation tile, and
+// warp, at most 32): the published scaled temperatures and request / answer /
+// waiting tags, each evaluator's 16 temperatures and 16 x 72 BF16 activation tile, and
 // the count of cell warps still running.
 constexpr int kNetActLd = 64 + 8;
 __host__ __device__ inline size_t net_cta_smem_bytes(int cells) {
-  return (size_t)32 * 4 * 3 + (size_t)net_evaluators(cells) * (16 * 4 + 16 * kNetActLd * 2) + 16;
+  return (size_t)32 * 4 * 4 + (size_t)net_evaluators(cells) * (16 * 4 + 16 * kNetActLd * 2) + 16;
 }
 }  // namespace stev

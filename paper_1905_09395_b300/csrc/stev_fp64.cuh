@@ -185,7 +185,7 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
 
 // ---------------------------------------------------------- persistent kernel
 template <int G>
-__global__ void __launch_bounds__(kMaxBlock) stev_fp64_kernel(Launch L) {
+__global__ void __launch_bounds__(kMaxBlock, 1) stev_fp64_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = L.S, R = L.R;
   // stage the mechanism tables once per CTA

@@ -47,6 +47,12 @@ struct TablesF {
   const float* tw;    // float twiddles
 };
 
+// T inside the network's training range (T > 0: compared on the bit patterns)
+__device__ __forceinline__ bool in_net_range(double T) {
+  const long long b = dbits(T);
+  return b >= dbits(kMlpTLow) && b <= dbits(kMlpTHigh);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -75,14 +81,16 @@ __device__ __forceinline__ double log1p_small(double u) {
 template <int G>
 __device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, const float* cYf,
                                             float* cH, const float* cTh,
-                                            const volatile int* net_ans, int net_tag,
+                                            volatile int* net_ans, int net_tag,
                                             bool use_net, double T, float Tf, float invTf, int l,
                                             float cpp) {
   const int S = L.S;
   if (use_net) {
     bool answered = *net_ans == net_tag;
+    if (!__all_sync(0xffffffffu, answered) && l == 0)
+      net_ans[32] = net_tag;  // waiting: the evaluator answers at once (row + 32 = wait tags)
     for (int k = 0; !answered && k < (1 << 18); ++k) {
-      __nanosleep(128);
+      __nanosleep(64);
       answered = *net_ans == net_tag;
     }
     answered = __all_sync(0xffffffffu, answered);
@@ -124,10 +132,10 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
                                           float* cYf, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
                                           CellState& st, const float* cTh,
-                                          const volatile int* net_ans, int net_tag) {
+                                          volatile int* net_ans, int net_tag) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
-  const bool use_net = MLP && T >= kMlpTLow && T <= kMlpTHigh;  // one cell per warp
+  const bool use_net = MLP && in_net_range(T);  // one cell per warp
   const double lnT = st.lnT;        // FP64: feeds G/RT
   const float Tf = (float)T;
   // 1/T in FP64: the FP32 reciprocal refined by two Newton steps (each squares
@@ -172,7 +180,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const float ghi = (float)g2;
     cG2[i] = make_float2(ghi, (float)(g2 - (double)ghi));  // g2 == hi + lo to ~2^-48
     const float y = fmaxf(Yi, 0.0f);
-    const float ys = (L.alpha > 0.0) ? y * __fdividef(y, (float)L.alpha + y) : y;
+    const float ys = (L.alpha_f > 0.0f) ? y * __fdividef(y, L.alpha_f + y) : y;
     cC[i] = rho * ys * spf[SPF_INVW];
   }
   float cpsum = 0.0f;
@@ -240,7 +248,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const float rstar = fmaxf(-ri, 1.0e-30f);
     const float Yi = cYf[i];
     const float ystar = (Yi < 1.0e-20f) ? 1.0f : 0.9f * Yi;
-    tmin = fminf(tmin, __fdividef(fminf((float)L.y_step_max, ystar), rstar));
+    tmin = fminf(tmin, __fdividef(fminf(L.y_step_max_f, ystar), rstar));
   }
   const float hw = group_sum<G>(hwp);
   tmin = group_min<G>(tmin);
@@ -256,8 +264,8 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   // ringing detection and damping (Eqs. 8-13), FP32
   if (L.dft_on) {
     const bool full = (st.nhist + 1 >= N);
-    const float tol_freq = (float)L.tol_freq, tol_ring = (float)L.tol_ring;
-    const float r_fac = (float)L.r_fac;
+    const float tol_freq = L.tol_freq_f, tol_ring = L.tol_ring_f;
+    const float r_fac = L.r_fac_f;
     for (int w = l; w < Rrev; w += G) {
       const float x = cHist[ktap * Rrev + w] * hf;
       cHist[ktap * Rrev + w] = x;
@@ -286,10 +294,10 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
               max2 = fmaxf(max2, fmaf(re, re, im * im));
             }
             const float d = D0 * inv;
-            if (d * d < tol_ring * tol_ring * max2) rstar = 1.0f / r_fac;
+            if (d * d < tol_ring * tol_ring * max2) rstar = L.inv_r_fac_f;
           }
         }
-        rof = fmaxf(fminf(rof * rstar, 1.0f), (float)L.rof_min);
+        rof = fmaxf(fminf(rof * rstar, 1.0f), L.rof_min_f);
       } else {
         rof = fminf(rof * r_fac, 1.0f);
       }
@@ -541,8 +549,9 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
   unsigned char* cells = smem_raw + tables;
   float* sT = reinterpret_cast<float*>(cells + (size_t)ncells * cell_bytes);
   int* tag_req = reinterpret_cast<int*>(sT + 32);
-  int* tag_ans = tag_req + 32;
-  float* ev_base = reinterpret_cast<float*>(tag_ans + 32);
+  int* tag_ans = tag_req + 32;   // then tag_wait at tag_ans + 32: a waiting cell's tag
+  int* tag_wait = tag_ans + 32;
+  float* ev_base = reinterpret_cast<float*>(tag_wait + 32);
   constexpr int kEvFloats = 16 + 16 * kNetActLd / 2;  // 16 temperatures + the BF16 tile
   int* s_active = reinterpret_cast<int*>(ev_base + nev * kEvFloats);
   // cell r's output row is at a fixed offset in its cell block: rows cell_bytes apart
@@ -551,6 +560,7 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
     sT[r] = 0.0f;
     tag_req[r] = 0;
     tag_ans[r] = 0;
+    tag_wait[r] = 0;
   }
   if (threadIdx.x == 0) *s_active = ncells;
   __syncthreads();
@@ -567,10 +577,11 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
     unsigned long long first = 0;  // when the oldest unanswered request was seen
     while (*(volatile int*)s_active > 0) {
       int req = 0;
-      bool fresh = false;
+      bool fresh = false, waiting = false;
       if (mine) {
         req = *(volatile int*)&tag_req[r];
         fresh = req != *(volatile int*)&tag_ans[r];
+        waiting = fresh && *(volatile int*)&tag_wait[r] == req;
       }
       const int nfresh = __popc(__ballot_sync(0xffffffffu, fresh));
       if (nfresh == 0) {
@@ -578,12 +589,13 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
         __nanosleep(128);
         continue;
       }
-      // batch: wait for 3/4 of the rows or until the oldest request is 4 us
-      // old (cells ask at the start of a step and need the answer near its end)
+      // batch: wait for 3/4 of the rows, a cell already waiting, or the oldest
+      // request 4 us old (cells ask at the start of a step and need the
+      // answer near its end)
       const unsigned long long now = __shfl_sync(0xffffffffu, gtimer_ns(), 0);
       if (first == 0) first = now;
-      if (4 * nfresh < 3 * nrow && now - first < 4000) {
-        __nanosleep(256);
+      if (4 * nfresh < 3 * nrow && !__any_sync(0xffffffffu, waiting) && now - first < 4000) {
+        __nanosleep(128);
         continue;
       }
       first = 0;
@@ -635,7 +647,7 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
     }
     idle_since = 0;
     idle_sleep = 1000u;
-    if (st.T >= kMlpTLow && st.T <= kMlpTHigh) {
+    if (in_net_range(st.T)) {
       ++tag;  // warp-uniform
       if (l == 0) {
         *(volatile float*)&sT[warp] = ((float)st.T - kTMid) / kTHalf;

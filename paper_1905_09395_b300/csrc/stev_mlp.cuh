@@ -253,6 +253,93 @@ __global__ void mlp_adam_kernel(float* __restrict__ p, const float* __restrict__
   p[k] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
 }
 
+// --------------------------------------- Levenberg-Marquardt (Sec. 3)
+// Jacobian of the standardised outputs with respect to every parameter, one
+// CTA of kHid threads per sample, and the residuals y - target.  Row
+// s * n_out + o of J (n_params floats, the flattened parameter order) is
+//   W1[k]: d1_k t,  b1[k]: d1_k,  W2[j][k]: d2_j a1_k,  b2[j]: d2_j,
+//   W3[o'][k]: a2_k if o' == o else 0,  b3[o']: 1 if o' == o else 0,
+// with d2_j = W3[o][j] (1 - a2_j^2) and d1_k = (1 - a1_k^2) sum_j W2[j][k] d2_j.
+__global__ void __launch_bounds__(kHid) mlp_jacobian_kernel(
+    const float* __restrict__ params, int n_out, const double* __restrict__ T,
+    const float* __restrict__ target, float* __restrict__ J, float* __restrict__ resid) {
+  __shared__ float a1[kHid], a2[kHid], d2[kHid];
+  const MlpOffsets off = mlp_offsets(n_out);
+  const int s = blockIdx.x, k = threadIdx.x;
+  const float t = ((float)T[s] - kTMid) / kTHalf;
+  a1[k] = tanhf(fmaf(params[off.W1 + k], t, params[off.b1 + k]));
+  __syncthreads();
+  float acc = params[off.b2 + k];
+  for (int i = 0; i < kHid; ++i) acc = fmaf(params[off.W2 + k * kHid + i], a1[i], acc);
+  a2[k] = tanhf(acc);
+  __syncthreads();
+  for (int o = 0; o < n_out; ++o) {
+    float* row = J + ((size_t)s * n_out + o) * off.total;
+    if (k == 0) {
+      float y = params[off.b3 + o];
+      for (int j = 0; j < kHid; ++j) y = fmaf(params[off.W3 + o * kHid + j], a2[j], y);
+      resid[(size_t)s * n_out + o] = y - target[(size_t)s * n_out + o];
+    }
+    d2[k] = params[off.W3 + o * kHid + k] * (1.0f - a2[k] * a2[k]);
+    __syncthreads();
+    float g = 0.0f;
+    for (int j = 0; j < kHid; ++j) g = fmaf(params[off.W2 + j * kHid + k], d2[j], g);
+    const float d1 = g * (1.0f - a1[k] * a1[k]);
+    row[off.W1 + k] = d1 * t;
+    row[off.b1 + k] = d1;
+    for (int j = 0; j < kHid; ++j) row[off.W2 + j * kHid + k] = d2[j] * a1[k];
+    row[off.b2 + k] = d2[k];
+    for (int q = k; q < n_out * kHid; q += kHid)
+      row[off.W3 + q] = (q / kHid == o) ? a2[q % kHid] : 0.0f;
+    for (int q = k; q < n_out; q += kHid) row[off.b3 + q] = (q == o) ? 1.0f : 0.0f;
+    __syncthreads();
+  }
+}
+
+// Squared error of each sample (FP32 forward, FP64 sum over its outputs).
+__global__ void mlp_sqerr_kernel(const float* __restrict__ params, int n_out,
+                                 const double* __restrict__ T, const float* __restrict__ target,
+                                 long long n, double* __restrict__ se) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const MlpOffsets off = mlp_offsets(n_out);
+  const float t = ((float)T[s] - kTMid) / kTHalf;
+  float a1[kHid], a2[kHid];
+  for (int k = 0; k < kHid; ++k) a1[k] = tanhf(fmaf(params[off.W1 + k], t, params[off.b1 + k]));
+  for (int j = 0; j < kHid; ++j) {
+    float acc = params[off.b2 + j];
+    for (int k = 0; k < kHid; ++k) acc = fmaf(params[off.W2 + j * kHid + k], a1[k], acc);
+    a2[j] = tanhf(acc);
+  }
+  double e = 0.0;
+  for (int o = 0; o < n_out; ++o) {
+    float y = params[off.b3 + o];
+    for (int j = 0; j < kHid; ++j) y = fmaf(params[off.W3 + o * kHid + j], a2[j], y);
+    const double d = (double)y - (double)target[s * n_out + o];
+    e += d * d;
+  }
+  se[s] = e;
+}
+
+// A (FP32, n x n, column-major lower part from SYRK) -> Ad (FP64, full lower
+// part) with Marquardt's damping on the diagonal: A_ii (1 + lambda) + eps.
+__global__ void mlp_damp_kernel(const float* __restrict__ A, int n, double lambda, double eps,
+                                double* __restrict__ Ad) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int c = (int)(idx / n), r = (int)(idx % n);
+  double v = r >= c ? (double)A[idx] : 0.0;
+  if (r == c) v = v * (1.0 + lambda) + eps;
+  Ad[idx] = v;
+}
+
+// p_new = p - (float)d
+__global__ void mlp_step_kernel(const float* __restrict__ p, const double* __restrict__ d, int n,
+                                float* __restrict__ p_new) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) p_new[k] = p[k] - (float)d[k];
+}
+
 // ------------------------------------------------------------- inference
 __device__ __forceinline__ float tanh_approx(float x) {
   float r;
