@@ -46,7 +46,7 @@ class _Mech(ctypes.Structure):
         ("t_range", ctypes.c_void_p), ("rxn_ptr", ctypes.c_void_p),
         ("rxn_species", ctypes.c_void_p), ("rxn_nu", ctypes.c_void_p),
         ("A", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("Ea", ctypes.c_void_p),
-        ("reversible", ctypes.c_void_p),
+        ("reversible", ctypes.c_void_p), ("rxn_order", ctypes.c_void_p),
     ]
 
 
@@ -142,10 +142,13 @@ class OracleMechanism:
             rxn_species=np.ascontiguousarray(mech.rxn_species, dtype=np.int32),
             rxn_nu=f64(mech.rxn_nu), A=f64(mech.A), beta=f64(mech.beta), Ea=f64(mech.Ea),
             reversible=np.ascontiguousarray(mech.reversible, dtype=np.uint8))
+        order = getattr(mech, "rxn_order", None)
+        if order is not None:
+            self._arrays["rxn_order"] = f64(order)
         a = self._arrays
         self.struct = _Mech(self.S, self.R, *(_ptr(a[k]) for k in (
             "mol_weight", "nasa7", "t_range", "rxn_ptr", "rxn_species", "rxn_nu", "A", "beta",
-            "Ea", "reversible")))
+            "Ea", "reversible")), _ptr(a["rxn_order"]) if "rxn_order" in a else None)
 
     @property
     def ref(self):

@@ -14,7 +14,8 @@
  *   oracle_thermo      Sec. 3, Eqs. 15-16 (cp/R, H/RT) and the standard
  *                      NASA-7 entropy form S/R (needed by dG of Eq. 30).
  *   oracle_rates       Sec. 2.2 Eqs. 6-7 (gamma stabilisation), Sec. 7.1
- *                      Eqs. 29-30 (mass action, Arrhenius, K from dG),
+ *                      Eqs. 28-30 (mass action or the real orders of global
+ *                      rate laws, Arrhenius, K from dG),
  *                      Eq. 14 (effective rate), Sec. 3 / Eq. 17 (the ODE
  *                      right-hand side including adiabatic temperature).
  *   oracle_step_size   Sec. 2.1 Eqs. 1-5.
@@ -80,6 +81,8 @@ typedef struct {
   const double *rxn_nu;              /* [nnz] */
   const double *A, *beta, *Ea;       /* [R] SI, J/mol */
   const unsigned char *reversible;   /* [R] */
+  const double *rxn_order;           /* [nnz] or NULL: the entry's order in the forward
+                                        (nu < 0) or reverse (nu > 0) rate; NULL = |nu| */
 } oracle_mech;
 
 typedef struct {
@@ -114,12 +117,18 @@ void oracle_thermo(const oracle_mech *m, double T, double *cpR, double *hRT, dou
 }
 
 static double int_power(double x, double nu) {
-  /* C^nu for the integer orders of elementary reactions (Sec. 4). */
+  /* C^a: repeated products for the integer orders of elementary reactions,
+   * pow for the real orders of global rate laws (Eqs. 28-29). */
   int n = (int)nu;
   if ((double)n != nu) return pow(x, nu);
   double p = 1.0;
   for (int k = 0; k < n; ++k) p *= x;
   return p;
+}
+
+/* Order of CSR entry k in its rate law: the given order, else |nu|. */
+static double entry_order(const oracle_mech *m, int k) {
+  return m->rxn_order ? m->rxn_order[k] : fabs(m->rxn_nu[k]);
 }
 
 /* ----------------------------------------------------------------- rates */
@@ -158,7 +167,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
     double fwd = kf, rev = 0.0;
     for (int k = m->rxn_ptr[r]; k < m->rxn_ptr[r + 1]; ++k) {
       double nu = m->rxn_nu[k];
-      if (nu < 0.0) fwd *= int_power(C[m->rxn_species[k]], -nu);
+      if (nu < 0.0) fwd *= int_power(C[m->rxn_species[k]], entry_order(m, k));
     }
     if (m->reversible[r]) {
       double dG = 0.0, dN = 0.0;
@@ -172,7 +181,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
       rev = kr;
       for (int k = m->rxn_ptr[r]; k < m->rxn_ptr[r + 1]; ++k) {
         double nu = m->rxn_nu[k];
-        if (nu > 0.0) rev *= int_power(C[m->rxn_species[k]], nu);
+        if (nu > 0.0) rev *= int_power(C[m->rxn_species[k]], entry_order(m, k));
       }
     }
     q[r] = ORACLE_Q(fwd - rev);

@@ -62,6 +62,9 @@ class Mechanism:
     reversible: np.ndarray    # [R] uint8
     seed: int = 0
     name: str = ""
+    # [nnz] float64 or None: each entry's order in the forward (reactants) or
+    # reverse (products) rate law; None = |nu| (mass action)
+    rxn_order: Optional[np.ndarray] = None
 
     @property
     def n_species(self) -> int:
@@ -319,3 +322,70 @@ def serving_requests(duration: float = 10.0, rate: float = 200.0, lo: int = 1000
         n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
         off = int(rng.integers(0, hi - n + 1))
         out.append((t, mi, n, off))
+
+
+# ----------------------------------------------------------------------------
+# the paper's BFER methane mechanism (Sec. 7.1, Eqs. 26-30, Table 1)
+# ----------------------------------------------------------------------------
+
+# species of the two-step mechanism and their standard formation enthalpies
+# and entropies at 298.15 K (textbook values; J/mol, J/mol/K)
+BFER_SPECIES = ("CH4", "O2", "CO", "H2O", "CO2", "N2")
+_BFER_ELEMENTS = np.array([[1, 4, 0, 0], [0, 0, 2, 0], [1, 0, 1, 0], [0, 2, 1, 0],
+                           [1, 0, 2, 0], [0, 0, 0, 2]], dtype=np.int64)
+_BFER_HF = np.array([-74.6e3, 0.0, -110.5e3, -241.8e3, -393.5e3, 0.0])
+_BFER_S298 = np.array([186.3, 205.2, 197.7, 188.8, 213.8, 191.6])
+CAL = 4.184  # J/cal
+
+
+def bfer_mechanism(seed: int = 5) -> Mechanism:
+    """The BFER two-step methane mechanism of Sec. 7.1: MEPOX
+    CH4 + 1.5 O2 -> CO + 2 H2O (irreversible, Eq. 28: orders 0.5 in CH4 and
+    0.65 in O2) and COROX CO + 0.5 O2 <=> CO2 (Eq. 29: T^0.7, orders 1 and 0.5
+    forward, 1 in CO2 backward, K from Eq. 30), with Table 1's constants
+    (cm-mol-s-cal) converted to SI; N2 is inert.  The paper gives no NASA-7
+    data, so each species' heat capacity is a seeded smooth curve (as for the
+    other synthetic mechanisms) with textbook formation enthalpy and entropy."""
+    rng = np.random.default_rng(seed)
+    S = len(BFER_SPECIES)
+    W = _BFER_ELEMENTS @ ATOMIC_MASS
+    nasa7 = np.stack([_fit_nasa7(rng, _BFER_HF[i], _BFER_S298[i]) for i in range(S)])
+    t_range = np.tile(np.array([T_LOW, T_SPLIT, T_HIGH]), (S, 1))
+    CH4, O2, CO, H2O, CO2 = 0, 1, 2, 3, 4
+    # CSR entries: species, nu, order (products of the irreversible MEPOX: order unused)
+    mepox = [(CH4, -1.0, 0.5), (O2, -1.5, 0.65), (CO, 1.0, 1.0), (H2O, 2.0, 2.0)]
+    corox = [(O2, -0.5, 0.5), (CO, -1.0, 1.0), (CO2, 1.0, 1.0)]
+    ptr, sp, nu, order = [0], [], [], []
+    for rx in (mepox, corox):
+        for s_, n_, o_ in sorted(rx):
+            sp.append(s_)
+            nu.append(n_)
+            order.append(o_)
+        ptr.append(len(sp))
+    fwd_order = np.array([0.5 + 0.65, 1.0 + 0.5])
+    A = np.array([4.9e9, 2.0e8]) * (1e-6) ** (fwd_order - 1.0)
+    return Mechanism(
+        elements=_BFER_ELEMENTS.copy(), mol_weight=W.astype(np.float64),
+        nasa7=nasa7.astype(np.float64), t_range=t_range.astype(np.float64),
+        rxn_ptr=np.array(ptr, dtype=np.int32), rxn_species=np.array(sp, dtype=np.int32),
+        rxn_nu=np.array(nu, dtype=np.float64), A=A, beta=np.array([0.0, 0.7]),
+        Ea=np.array([35500.0, 12000.0]) * CAL, reversible=np.array([0, 1], dtype=np.uint8),
+        seed=seed, name="bfer", rxn_order=np.array(order, dtype=np.float64))
+
+
+def bfer_cells(mech: Mechanism, n_cells: int, seed: int = 6,
+               T_range: Tuple[float, float] = (1200.0, 2200.0)):
+    """Random fixed thermochemical states as in the paper's BFER benchmark
+    (Sec. 7.1): T0 uniform, 1 atm, a methane-air-like mixture with products
+    (CH4 0-0.1, O2 0.05-0.23, CO and CO2 0-0.05, H2O 0-0.1, the rest N2)."""
+    rng = np.random.default_rng(seed + 7919)
+    T = rng.uniform(T_range[0], T_range[1], size=n_cells)
+    P = np.full(n_cells, P_ATM)
+    Y = np.zeros((n_cells, mech.n_species))
+    Y[:, 0] = rng.uniform(0.0, 0.1, n_cells)
+    Y[:, 1] = rng.uniform(0.05, 0.23, n_cells)
+    Y[:, 2] = rng.uniform(0.0, 0.05, n_cells)
+    Y[:, 3] = rng.uniform(0.0, 0.1, n_cells)
+    Y[:, 4] = rng.uniform(0.0, 0.05, n_cells)
+    Y[:, 5] = 1.0 - Y[:, :5].sum(axis=1)
+    return T, P, Y
