@@ -43,10 +43,11 @@ EXP_OPS, LOG_OPS, DIV_OPS = 16.0, 30.0, 7.5
 # FP64 pipe peak: 1.667 DFMA/clk/SM x 148 SMs at the probe's 1919 MHz under load
 FP64_PEAK_OPS = 4.733e11
 # DRAM bytes per cell of one launch, from the ncu captures summarised in
-# profiles/ (3,108- and 1,628-cell cases; reads only: the small cases' output
-# writes stay in L2), scaled to the full launch by the cells it processes.
-# Set to None when the kernel changes after the capture.
-DRAM_BYTES_PER_CELL = {"mixed": 924160 / 3108, "fp64": 528896 / 1628, "mixed+mlp": None}
+# profiles/ (3,108-, 2,960- and 1,628-cell cases of 300 steps; reads only: the
+# small cases' output writes stay in L2), scaled to the full launch by the
+# cells it processes.  Set to None when the kernel changes after the capture.
+DRAM_BYTES_PER_CELL = {"mixed": 929024 / 3108, "fp64": 530688 / 1628,
+                       "mixed+mlp": 910336 / 2960}
 
 
 def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
@@ -205,7 +206,11 @@ def oracle_error(gpu, ref, tol_Y, tol_T):
             "within_target": float(np.mean((dY <= tol_Y) & (dT <= tol_T))),
             "median_dY": float(np.median(dY)), "max_dY": float(dY.max()),
             "median_dT_K": float(np.median(dT)), "max_dT_K": float(dT.max()),
-            "status_equal": float(np.mean(gpu[3][:n] == ref[3][:n]))}
+            "status_equal": float(np.mean(gpu[3][:n] == ref[3][:n])),
+            "note": "raw comparison on the first cells of the workload; on the 32/150 "
+                    "mechanism the oracle moves nearly every cell by more than 1e-10 under a "
+                    "one-ulp change of its rates, so the 1e-8 bar is checked in the tests on "
+                    "step prefixes and on well-conditioned cells"}
 
 
 def run_reference(args):
@@ -502,6 +507,76 @@ def run_serve(args):
     return 0
 
 
+def run_bfer(args):
+    """The paper's own single-phase benchmark shape (Sec. 7.1): the BFER
+    methane mechanism (6 species, 2 global reactions with real orders, Table 1
+    constants) on random fixed states, t_f = 1 ms; one solve of all cells per
+    step, for plain FP64, mixed precision with NASA-7 thermo and mixed with the
+    thermo network (trained on the GPU before timing)."""
+    import torch
+    from paper_1905_09395_b300 import Mechanism, binding, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    mech = synth.bfer_mechanism()
+    T, P, Y = synth.bfer_cells(mech, args.cells)
+    n = len(T)
+    Td, Pd, Yd = (torch.from_numpy(a).to(dev) for a in (T, P, Y))
+    out = (torch.empty_like(Td), torch.empty_like(Yd), torch.empty(n, dtype=torch.int32, device=dev),
+           torch.empty(n, dtype=torch.uint8, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    arms = {}
+    with ClockSampler(0) as clk:
+        for name, kw in (("mixed+mlp", dict(precision=binding.MIXED)),
+                         ("mixed_poly", dict(precision=binding.MIXED)),
+                         ("plain_fp64", dict(precision=binding.FP64))):
+            m = Mechanism(mech, **kw)
+            info = None
+            if name == "mixed+mlp":
+                t0 = time.time()
+                Ts = np.random.default_rng(2024).uniform(300.0, 3000.0, size=args.mlp_samples)
+                hist = m.mlp_train(Ts, epochs=args.mlp_epochs, batch=4096, lr=2e-3, seed=7)
+                m.set_options(thermo=binding.THERMO_MLP)
+                info = {"final_loss": float(hist[-1]), "train_s": time.time() - t0}
+            ms, _, _ = timed_solves(m, Td, Pd, Yd, 1e-3, out, args.steps, args.warmup,
+                                    args.warmup_cells, stream)
+            it = out[2].cpu().numpy().astype(np.int64)
+            st = np.bincount(out[3].cpu().numpy(), minlength=4)
+            arms[name] = {"value": n / (float(np.mean(ms)) / 1e3), "unit": UNIT,
+                          "ms_per_step": float(np.mean(ms)),
+                          "cell_steps_per_s": float(it.sum()) / (float(np.mean(ms)) / 1e3),
+                          "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+                          "cell_status": st.tolist(), "resident_slots": m.resident_slots,
+                          "thermo_net": info}
+            head = [x[:4096].cpu().numpy() for x in out]
+            arms[name]["_head"] = head
+            m.close()
+        clocks = clk.summary()
+    keep = {}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(mech, T, P, Y, 1e-3, keep=keep)
+    for name, a in arms.items():
+        head = a.pop("_head")
+        if cpu is not None:
+            fp64 = name == "plain_fp64"
+            a["oracle_error"] = oracle_error(head, keep["ref"], 1e-8 if fp64 else 1e-4,
+                                             1e-6 if fp64 else 0.5)
+    h = arms["mixed+mlp"]
+    line = {"metric": "cell-solves/s, BFER methane mechanism (Sec. 7.1), random fixed states, "
+                      "t_f = 1 ms", "value": h["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "bfer: 6 species (CH4 O2 CO H2O CO2 N2), MEPOX + COROX with "
+                                   "Table 1 constants, %d cells, T0 U[1200,2200] K, 1 atm, "
+                                   "methane-air-like Y0, dt 1e-3 s" % n,
+                       "l2": "inputs (%d MB) %s L2" % ((T.nbytes + P.nbytes + Y.nbytes) >> 20,
+                                                       "larger than" if n >= (1 << 19) else
+                                                       "within")},
+            "arms": arms, "gpu_launches": 3 * (args.steps + args.warmup), "clocks": clocks,
+            "cpu_baseline": cpu}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_1905_09395_b300 import Mechanism, binding
@@ -670,9 +745,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["scale", "uneven", "serve"], default="scale",
+    ap.add_argument("--workload", choices=["scale", "uneven", "serve", "bfer"], default="scale",
                     help="uneven: 64 uneven 53/325 batches in one batched launch; serve: "
-                         "the request loop, mixed+MLP and plain FP64")
+                         "the request loop, mixed+MLP and plain FP64; bfer: the paper's "
+                         "BFER methane mechanism on random states")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window")
     ap.add_argument("--serve-drain", type=float, default=5.0,
@@ -706,6 +782,8 @@ def main(argv=None):
         return run_uneven(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "bfer":
+        return run_bfer(args)
     return run_ours(args)
 
 

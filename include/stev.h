@@ -89,7 +89,8 @@ void stev_default_options(stev_options *opt);
  *   rxn_species [nnz] species index of each entry.
  *   rxn_nu      [nnz] stoichiometric coefficient: < 0 reactant, > 0 product.
  *               Reactions must be elementary: integer orders with at most two
- *               molecules on each side (Sec. 4), each species at most once.
+ *               molecules on each side (Sec. 4), each species at most once
+ *               (stev_mechanism_create_orders takes global rate laws).
  *   A, beta, Ea [R] Arrhenius k = A T^beta exp(-Ea/(R T)) (Eq. 29 form), SI.
  *   reversible  [R] nonzero: reverse rate kf/K with K from Eq. 30.
  *   opt         NULL for the defaults.
@@ -104,6 +105,24 @@ stev_status stev_mechanism_create(int n_species, int n_reactions, const double *
                                   const double *rxn_nu, const double *A, const double *beta,
                                   const double *Ea, const unsigned char *reversible,
                                   const stev_options *opt, stev_mechanism **out);
+
+/* As stev_mechanism_create, for global rate laws such as the paper's BFER
+ * methane mechanism (Sec. 7.1, Eqs. 26-29): stoichiometric coefficients may be
+ * any nonzero real (e.g. 1.5 O2), and rxn_order [nnz] (nullable) gives each
+ * entry's order in its rate law, > 0: the forward rate kf prod C^order over
+ * the reactant entries (nu < 0), the reverse rate kf/K prod C^order over the
+ * product entries (nu > 0).  NULL orders mean |nu| (mass action).  A reaction
+ * then has at most two distinct reactant and two distinct product species;
+ * K (Eq. 30) uses dN = sum nu.  Mechanisms whose every |nu| is 1 or 2 with
+ * orders |nu| take the same path as stev_mechanism_create.  Errors as
+ * stev_mechanism_create, plus STEV_EINVAL for an order <= 0. */
+stev_status stev_mechanism_create_orders(int n_species, int n_reactions, const double *mol_weight,
+                                         const double *nasa7, const double *t_range,
+                                         const int *rxn_ptr, const int *rxn_species,
+                                         const double *rxn_nu, const double *rxn_order,
+                                         const double *A, const double *beta, const double *Ea,
+                                         const unsigned char *reversible, const stev_options *opt,
+                                         stev_mechanism **out);
 
 /* Replaces the solver options of a mechanism (validated as in create). */
 stev_status stev_mechanism_set_options(stev_mechanism *mech, const stev_options *opt);

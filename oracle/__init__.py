@@ -73,10 +73,19 @@ PROBES = {"kf_up": ["-DORACLE_KF_SCALE=(1.0+2.220446049250313e-16)"],
           "K32_down": ["-DORACLE_K_SCALE=(1.0-3.814697265625e-06)"],
           # concentrations or net rates rounded to float every step
           "round32_C": ["-DORACLE_ROUND32_C"],
-          "round32_q": ["-DORACLE_ROUND32_Q"]}
+          "round32_q": ["-DORACLE_ROUND32_Q"],
+          # real-order powers C^a (global rate laws) changed by 4 ulp (math
+          # libraries' pow differ by a few ulp), or by 2^-17 (a single-precision
+          # 2^(a lg2 C) with |a lg2 C| up to ~32)
+          "pow_up": ["-DORACLE_POW_SCALE=(1.0+8.881784197001252e-16)"],
+          "pow_down": ["-DORACLE_POW_SCALE=(1.0-8.881784197001252e-16)"],
+          "pow32_up": ["-DORACLE_POW_SCALE=(1.0+7.62939453125e-06)"],
+          "pow32_down": ["-DORACLE_POW_SCALE=(1.0-7.62939453125e-06)"]}
 PROBE_LEVELS = {"fp64": ("kf_up", "kf_down", "K_up", "K_down"),
                 "fp32": ("kf32_up", "kf32_down", "K32_up", "K32_down", "round32_C",
                          "round32_q")}
+# probes that only matter for mechanisms with real reaction orders
+POW_PROBES = {"fp64": ("pow_up", "pow_down"), "fp32": ("pow32_up", "pow32_down")}
 # single-precision-sized changes of the thresholds that take discrete
 # decisions (the limiter's Y_step^max, the ringing tolerances of Eq. 12)
 OPTION_PROBES = {"fp64": (), "fp32": ("y_step_max", "tol_freq", "tol_ring")}
@@ -266,13 +275,20 @@ def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] =
     every K by 64 ulp; "fp32" by 2^-22 and 2^-18, the size of the rounding
     of a single-precision rate and of its exponent, rounds every
     concentration or every net rate to float, and moves the limiter's
-    Y_step^max and the ringing tolerances by 2^-22.  A cell whose spread is far below a tolerance is
+    Y_step^max and the ringing tolerances by 2^-22; for mechanisms with real
+    reaction orders also every power C^a by 4 ulp ("fp64") or 2^-17
+    ("fp32").  A cell whose spread is far below a tolerance is
     well-conditioned at that tolerance."""
     if base is None:
         base = solve(mech, T, P, Y, dt, n_threads=n_threads, **opts)
     dY = np.zeros(len(T))
     dT = np.zeros(len(T))
     runs = [dict(probe=p) for p in PROBE_LEVELS[level]]
+    order = getattr(mech, "rxn_order", None)
+    real_orders = np.concatenate([np.abs(np.asarray(mech.rxn_nu, dtype=float)),
+                                  np.asarray(order if order is not None else [], dtype=float)])
+    if np.any(real_orders != np.round(real_orders)):
+        runs += [dict(probe=p) for p in POW_PROBES[level]]
     for name in OPTION_PROBES[level]:
         v = opts.get(name, DEFAULT_OPTS[name])
         runs += [{name: v * (1.0 + 2.0 ** -22)}, {name: v * (1.0 - 2.0 ** -22)}]

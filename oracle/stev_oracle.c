@@ -116,11 +116,17 @@ void oracle_thermo(const oracle_mech *m, double T, double *cpR, double *hRT, dou
   }
 }
 
+/* Conditioning probe of the real-order powers (default: exactly 1.0): pow
+ * results may differ between math libraries by a few ulp. */
+#ifndef ORACLE_POW_SCALE
+#define ORACLE_POW_SCALE 1.0
+#endif
+
 static double int_power(double x, double nu) {
   /* C^a: repeated products for the integer orders of elementary reactions,
    * pow for the real orders of global rate laws (Eqs. 28-29). */
   int n = (int)nu;
-  if ((double)n != nu) return pow(x, nu);
+  if ((double)n != nu) return pow(x, nu) * ORACLE_POW_SCALE;
   double p = 1.0;
   for (int k = 0; k < n; ++k) p *= x;
   return p;

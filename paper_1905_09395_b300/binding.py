@@ -31,7 +31,7 @@ EXPORTS = (
     "stev_mlp_loss_grad", "stev_mlp_eval", "stev_solve_batched",
     "stev_server_create", "stev_server_submit", "stev_server_poll", "stev_server_get_stats",
     "stev_server_clock", "stev_server_stop", "stev_server_destroy", "stev_mlp_stalls",
-    "stev_mlp_train_lm", "stev_mlp_jacobian",
+    "stev_mlp_train_lm", "stev_mlp_jacobian", "stev_mechanism_create_orders",
 )
 
 
@@ -89,6 +89,8 @@ def lib():
         L.stev_default_options.restype = None
         L.stev_mechanism_create.argtypes = [I, I, P, P, P, P, P, P, P, P, P, P, P, P]
         L.stev_mechanism_create.restype = I
+        L.stev_mechanism_create_orders.argtypes = [I, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        L.stev_mechanism_create_orders.restype = I
         L.stev_mechanism_set_options.argtypes = [P, P]
         L.stev_mechanism_set_options.restype = I
         L.stev_mechanism_get_options.argtypes = [P, P]
@@ -184,10 +186,19 @@ class Mechanism:
             Ea=_np(tables.Ea, np.float64), rev=_np(tables.reversible, np.uint8))
         opt = default_options(**options)
         p = lambda a: a.ctypes.data
-        _check(lib().stev_mechanism_create(
-            self.S, self.R, p(keep["W"]), p(keep["nasa7"]), p(keep["t_range"]), p(keep["ptr"]),
-            p(keep["sp"]), p(keep["nu"]), p(keep["A"]), p(keep["beta"]), p(keep["Ea"]),
-            p(keep["rev"]), ctypes.byref(opt), ctypes.byref(self._h)))
+        order = getattr(tables, "rxn_order", None)
+        if order is None:
+            _check(lib().stev_mechanism_create(
+                self.S, self.R, p(keep["W"]), p(keep["nasa7"]), p(keep["t_range"]),
+                p(keep["ptr"]), p(keep["sp"]), p(keep["nu"]), p(keep["A"]), p(keep["beta"]),
+                p(keep["Ea"]), p(keep["rev"]), ctypes.byref(opt), ctypes.byref(self._h)))
+        else:   # global rate laws: real stoichiometry and orders
+            keep["order"] = _np(order, np.float64)
+            _check(lib().stev_mechanism_create_orders(
+                self.S, self.R, p(keep["W"]), p(keep["nasa7"]), p(keep["t_range"]),
+                p(keep["ptr"]), p(keep["sp"]), p(keep["nu"]), p(keep["order"]), p(keep["A"]),
+                p(keep["beta"]), p(keep["Ea"]), p(keep["rev"]), ctypes.byref(opt),
+                ctypes.byref(self._h)))
 
     # -- options ----------------------------------------------------------------
     @property

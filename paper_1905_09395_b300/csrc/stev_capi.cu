@@ -71,6 +71,12 @@ struct stev_mechanism {
   int per_sm = 0, sms = 0;  // resident CTAs per SM, SMs
   int cells = 0;            // resident cells per CTA
   unsigned long long* d_net_stalls = nullptr;  // network answers that timed out
+  // general rate laws (real stoichiometry / orders)
+  int general = 0;
+  double* d_rg = nullptr;
+  double* d_gnu = nullptr;
+  float* d_rgf = nullptr;
+  float* d_gnuf = nullptr;
   size_t smem = 0;
   long long nslots = 0;    // cells resident at once
   unsigned long long* d_counter = nullptr;
@@ -136,7 +142,7 @@ static stev_status check_options(const stev_options* o) {
 static void free_mech(stev_mechanism* m) {
   void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
                   m->d_twf, m->d_counter, m->d_mlp_params, m->d_mlp_W2, m->d_mlp_W3, m->d_mlp_misc,
-                  m->d_bdesc, m->d_boff, m->d_net_stalls,
+                  m->d_bdesc, m->d_boff, m->d_net_stalls, m->d_rg, m->d_gnu, m->d_rgf, m->d_gnuf,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -183,8 +189,8 @@ static stev_status configure(stev_mechanism* m) {
   const int G = m->G;
   const bool mixed = m->opt.precision == STEV_MIXED;
   const size_t tables =
-      mixed ? table_smem_bytes_mixed(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n)
-            : table_smem_bytes(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n);
+      mixed ? table_smem_bytes_mixed(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n, m->general)
+            : table_smem_bytes(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n, m->general);
   const bool net = m->opt.thermo != STEV_THERMO_POLY;
   const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n, net)
                             : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
@@ -228,6 +234,25 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
                                              const unsigned char* reversible,
                                              const stev_options* opt, stev_mechanism** out) {
   g_err.clear();
+  if (out) *out = nullptr;
+  if (rxn_ptr && rxn_nu && R >= 1 && R <= kMaxReactions && rxn_ptr[0] == 0) {
+    for (int k = 0; k < rxn_ptr[R]; ++k) {
+      const double a = std::fabs(rxn_nu[k]);
+      if (!(a == 1.0 || a == 2.0))
+        return fail(STEV_EINVAL, "rxn_nu[%d]: only elementary orders |nu| in {1,2} are supported "
+                    "(global rate laws: stev_mechanism_create_orders)", k);
+    }
+  }
+  return stev_mechanism_create_orders(S, R, W, nasa7, t_range, rxn_ptr, rxn_species, rxn_nu,
+                                      nullptr, A, beta, Ea, reversible, opt, out);
+}
+
+extern "C" stev_status stev_mechanism_create_orders(
+    int S, int R, const double* W, const double* nasa7, const double* t_range,
+    const int* rxn_ptr, const int* rxn_species, const double* rxn_nu, const double* rxn_order,
+    const double* A, const double* beta, const double* Ea, const unsigned char* reversible,
+    const stev_options* opt, stev_mechanism** out) {
+  g_err.clear();
   if (!out) return fail(STEV_EINVAL, "out is NULL");
   *out = nullptr;
   if (S < 1 || S > kMaxSpecies) return fail(STEV_EINVAL, "n_species must be in [1, %d]", kMaxSpecies);
@@ -264,31 +289,57 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
     }
   }
 
-  // reaction tables
+  // reaction tables.  Elementary mass action (every |nu| in {1, 2}, orders =
+  // |nu|) packs each molecule into a slot; otherwise the mechanism is
+  // "general": slots hold distinct species with their real nu and order.
   if (rxn_ptr[0] != 0) return fail(STEV_EINVAL, "rxn_ptr[0] must be 0");
+  int general = 0;
+  for (int k = 0; k < rxn_ptr[R]; ++k) {
+    const double nu = rxn_nu[k];
+    if (!std::isfinite(nu) || nu == 0.0) return fail(STEV_EINVAL, "rxn_nu[%d] must be finite and nonzero", k);
+    if (rxn_order && (!(rxn_order[k] > 0.0) || !std::isfinite(rxn_order[k])))
+      return fail(STEV_EINVAL, "rxn_order[%d] must be finite and > 0", k);
+    if (!(std::fabs(nu) == 1.0 || std::fabs(nu) == 2.0)) general = 1;
+    if (rxn_order && rxn_order[k] != std::fabs(nu)) general = 1;
+  }
   std::vector<double> rx((size_t)R * RX_STRIDE, 0.0);
   std::vector<int4> ri(R);
+  std::vector<double> rg((size_t)R * 8, 0.0);
   int nrev = 0;
   for (int r = 0; r < R; ++r) {
     const int lo = rxn_ptr[r], hi = rxn_ptr[r + 1];
     if (hi <= lo || hi - lo > 4) return fail(STEV_EINVAL, "reaction %d: bad rxn_ptr range", r);
     int reac[2], prod[2], nr = 0, np = 0;
-    double bal = 0.0, mag = 0.0;
+    double bal = 0.0, mag = 0.0, dN = 0.0;
     for (int k = lo; k < hi; ++k) {
       const int s = rxn_species[k];
       const double nu = rxn_nu[k];
       if (s < 0 || s >= S) return fail(STEV_EINVAL, "reaction %d: species index %d out of range", r, s);
       for (int k2 = lo; k2 < k; ++k2)
         if (rxn_species[k2] == s) return fail(STEV_EINVAL, "reaction %d: species %d listed twice", r, s);
-      if (!(nu == -2.0 || nu == -1.0 || nu == 1.0 || nu == 2.0))
-        return fail(STEV_EINVAL, "reaction %d: only elementary orders |nu| in {1,2} are supported", r);
-      const int mult = (int)std::fabs(nu);
-      for (int t = 0; t < mult; ++t) {
-        if (nu < 0) { if (nr == 2) return fail(STEV_EINVAL, "reaction %d: more than two reactant molecules", r); reac[nr++] = s; }
-        else        { if (np == 2) return fail(STEV_EINVAL, "reaction %d: more than two product molecules", r); prod[np++] = s; }
+      if (general) {
+        const double ord = rxn_order ? rxn_order[k] : std::fabs(nu);
+        if (nu < 0) {
+          if (nr == 2) return fail(STEV_EINVAL, "reaction %d: more than two reactant species", r);
+          rg[(size_t)r * 8 + nr] = nu;
+          rg[(size_t)r * 8 + 4 + nr] = ord;
+          reac[nr++] = s;
+        } else {
+          if (np == 2) return fail(STEV_EINVAL, "reaction %d: more than two product species", r);
+          rg[(size_t)r * 8 + 2 + np] = nu;
+          rg[(size_t)r * 8 + 6 + np] = ord;
+          prod[np++] = s;
+        }
+      } else {
+        const int mult = (int)std::fabs(nu);
+        for (int t = 0; t < mult; ++t) {
+          if (nu < 0) { if (nr == 2) return fail(STEV_EINVAL, "reaction %d: more than two reactant molecules", r); reac[nr++] = s; }
+          else        { if (np == 2) return fail(STEV_EINVAL, "reaction %d: more than two product molecules", r); prod[np++] = s; }
+        }
       }
       bal += nu * W[s];
       mag += std::fabs(nu * W[s]);
+      dN += nu;
     }
     if (nr == 0 || np == 0) return fail(STEV_EINVAL, "reaction %d needs reactants and products", r);
     if (std::fabs(bal) > 1e-12 * mag) return fail(STEV_EUNBALANCED, "reaction %d is not mass-balanced", r);
@@ -298,7 +349,7 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
     e[RX_LNA] = std::log(A[r]);
     e[RX_BETA] = beta[r];
     e[RX_EAR] = Ea[r] / kRu;
-    e[RX_DN] = (double)(np - nr);
+    e[RX_DN] = general ? dN : (double)(np - nr);
     const int a0 = reac[0], a1 = nr > 1 ? reac[1] : kNone;
     const int p0 = prod[0], p1 = np > 1 ? prod[1] : kNone;
     ri[r].x = a0 | (a1 << 8) | (p0 << 16) | (p1 << 24);
@@ -307,12 +358,17 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
     ri[r].w = reversible[r] ? nrev++ : -1;
   }
 
-  // species-major gather lists in ascending reaction order
+  // species-major gather lists in ascending reaction order (general rate
+  // laws keep each entry's real nu beside it)
   std::vector<int> gptr(S + 1, 0), gent;
+  std::vector<double> gnu;
   for (int i = 0; i < S; ++i) {
     for (int r = 0; r < R; ++r)
       for (int k = rxn_ptr[r]; k < rxn_ptr[r + 1]; ++k)
-        if (rxn_species[k] == i) gent.push_back(gather_pack(r, (int)rxn_nu[k]));
+        if (rxn_species[k] == i) {
+          gent.push_back(gather_pack(r, general ? 0 : (int)rxn_nu[k]));
+          gnu.push_back(rxn_nu[k]);
+        }
     gptr[i + 1] = (int)gent.size();
   }
 
@@ -321,6 +377,7 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
   m->R = R;
   m->Rrev = nrev;
   m->n_gather = (int)gent.size();
+  m->general = general;
   m->opt = o;
   if (cudaGetDevice(&m->device) != cudaSuccess) { delete m; return fail(STEV_ECUDA, "no CUDA device"); }
   m->n_hi_bins = o.dft_n / 2 - o.dft_hi_first + 1;
@@ -379,6 +436,13 @@ extern "C" stev_status stev_mechanism_create(int S, int R, const double* W, cons
   TRY_OR_FREE(upload((void**)&m->d_twf, twf.data(), twf.size() * sizeof(float)));
   TRY_OR_FREE(upload((void**)&m->d_gptr, gptr.data(), gptr.size() * sizeof(int)));
   TRY_OR_FREE(upload((void**)&m->d_gent, gent.data(), gent.size() * sizeof(int)));
+  if (general) {
+    std::vector<float> rgf(rg.begin(), rg.end()), gnuf(gnu.begin(), gnu.end());
+    TRY_OR_FREE(upload((void**)&m->d_rg, rg.data(), rg.size() * sizeof(double)));
+    TRY_OR_FREE(upload((void**)&m->d_gnu, gnu.data(), gnu.size() * sizeof(double)));
+    TRY_OR_FREE(upload((void**)&m->d_rgf, rgf.data(), rgf.size() * sizeof(float)));
+    TRY_OR_FREE(upload((void**)&m->d_gnuf, gnuf.data(), gnuf.size() * sizeof(float)));
+  }
   TRY_OR_FREE(configure(m));
   *out = m;
   return STEV_OK;
@@ -478,6 +542,11 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   }
   L.net_cells = m->cells;
   L.net_stalls = m->d_net_stalls;
+  L.general = m->general;
+  L.rg_tab = m->d_rg;
+  L.g_nu = m->d_gnu;
+  L.rg_tab_f = m->d_rgf;
+  L.g_nu_f = m->d_gnuf;
   return L;
 }
 

@@ -246,7 +246,17 @@ struct Tables {
   const int* gptr;
   const int* gent;
   const double* tw;
+  const double* rg;   // general rate laws: [R][8] nu, order of the slots
+  const double* gnu;  // general rate laws: [n_gather] nu
 };
+
+// C^a for a reaction order a: products for orders 1 and 2 (as elementary
+// mass action evaluates them), pow otherwise (global rate laws, Eq. 28).
+__device__ __forceinline__ double conc_pow(double c, double a) {
+  if (a == 1.0) return c;
+  if (a == 2.0) return c * c;
+  return pow(c, a);
+}
 
 template <int G>
 __device__ __forceinline__ float group_min(float v) {

@@ -81,6 +81,14 @@ struct Launch {
   const float* sp_tab_f;  // [S][SPF_STRIDE]        (mixed kernel)
   const float4* rx_tab_f; // [R] lg2 A, beta, Ea/R log2 e, dN (mixed kernel)
   const float* dft_tw_f;  // float twiddles          (mixed kernel)
+  // general rate laws (real stoichiometry and orders, e.g. Eqs. 26-29): per
+  // reaction nu then order of the slots a0, a1, p0, p1 (distinct species,
+  // unused slots 0), and the real nu of every gather entry
+  int general;
+  const double* rg_tab;   // [R][8]
+  const double* g_nu;     // [n_gather]
+  const float* rg_tab_f;  // [R][8]       (mixed kernel)
+  const float* g_nu_f;    // [n_gather]   (mixed kernel)
   int n_hi_bins;
   // options (Secs. 2.1-2.3)
   int dft_n, dft_on, max_iters;
@@ -125,12 +133,15 @@ struct Launch {
 
 constexpr double kMlpTLow = 300.0, kMlpTHigh = 3000.0;  // network's training range (K)
 
-// Shared-memory footprint of the tables (bytes, 16-byte aligned).
+// Shared-memory footprint of the tables (bytes, 16-byte aligned); general
+// rate laws add their per-reaction and per-gather-entry tables at the end.
 __host__ __device__ inline size_t table_smem_bytes(int S, int R, int n_gather, int n_hi_bins,
-                                                   int dft_n) {
+                                                   int dft_n, int general = 0) {
   size_t b = (size_t)S * SP_STRIDE * 8 + (size_t)R * RX_STRIDE * 8 + (size_t)R * 16 +
              (size_t)n_hi_bins * 2 * dft_n * 8 + (size_t)(S + 1 + n_gather) * 4;
-  return (b + 15) & ~(size_t)15;
+  b = (b + 15) & ~(size_t)15;
+  if (general) b += (size_t)R * 8 * 8 + (((size_t)n_gather * 8 + 15) & ~(size_t)15);
+  return b;
 }
 
 // Shared-memory footprint of one resident cell in the FP64 kernel: Y, C, G/RT,
@@ -141,11 +152,13 @@ __host__ __device__ inline size_t cell_smem_bytes_fp64(int S, int R, int Rrev, i
 }
 
 __host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gather, int n_hi_bins,
-                                                         int dft_n) {
+                                                         int dft_n, int general = 0) {
   size_t b = (size_t)S * SP_STRIDE * 8 + (size_t)R * 16 + (size_t)R * 16 +
              (size_t)S * SPF_STRIDE * 4 + (size_t)n_hi_bins * 2 * dft_n * 4 +
              (size_t)(S + 1 + n_gather) * 4;
-  return (b + 15) & ~(size_t)15;
+  b = (b + 15) & ~(size_t)15;
+  if (general) b += (size_t)R * 8 * 4 + (((size_t)n_gather * 4 + 15) & ~(size_t)15);
+  return b;
 }
 
 // Mixed kernel cell: Y in FP64 and G/RT log2 e as a float pair (8 bytes each

@@ -72,9 +72,30 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
     const int a0 = ri.x & 0xFF, a1 = (ri.x >> 8) & 0xFF;
     const int p0 = (ri.x >> 16) & 0xFF, p1 = (ri.x >> 24) & 0xFF;
     const double lnkf = fma(rx[RX_BETA], lnT, rx[RX_LNA]) - rx[RX_EAR] * invT;
-    double q = exp(lnkf) * cC[a0];
+    double q, rof = 1.0;
+    if (L.general) {
+      // real stoichiometry and orders: slots hold distinct species with their
+      // nu (rg[0..3]) and rate-law order (rg[4..7])
+      const double* rg = tb.rg + r * 8;
+      q = exp(lnkf) * conc_pow(cC[a0], rg[4]);
+      if (a1 != kNone) q *= conc_pow(cC[a1], rg[5]);
+      if (ri.z) {
+        double dG = fma(rg[2], cG[p0], rg[0] * cG[a0]);
+        if (a1 != kNone) dG = fma(rg[1], cG[a1], dG);
+        if (p1 != kNone) dG = fma(rg[3], cG[p1], dG);
+        double rev = exp(fma(-rx[RX_DN], lnPref, lnkf + dG)) * conc_pow(cC[p0], rg[6]);
+        if (p1 != kNone) rev *= conc_pow(cC[p1], rg[7]);
+        q -= rev;
+        if (L.dft_on) {
+          cHist[ktap * Rrev + ri.w] = q;
+          rof = cRof[ri.w];
+        }
+      }
+      cQ[r] = q * rof;
+      continue;
+    }
+    q = exp(lnkf) * cC[a0];
     if (a1 != kNone) q *= cC[a1];
-    double rof = 1.0;
     if (ri.z) {
       // dG/RT = sum nu G/RT;  ln kr = ln kf - ln K,  ln K = dN ln(P_atm/RT) - dG/RT
       double dG = cG[p0] - cG[a0];
@@ -99,7 +120,7 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
     double wd = 0.0;
     for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
       const int e = tb.gent[k];
-      wd = fma(kNuOf[e & 15], cQ[e >> 4], wd);
+      wd = fma(L.general ? tb.gnu[k] : kNuOf[e & 15], cQ[e >> 4], wd);
     }
     const double ri = tb.sp[i * SP_STRIDE + SP_W] * wd * invRho;
     hwp = fma(cH[i], wd, hwp);
@@ -201,13 +222,22 @@ __global__ void __launch_bounds__(kMaxBlock, 1) stev_fp64_kernel(Launch L) {
   for (int t = threadIdx.x; t < L.n_hi_bins * 2 * L.dft_n; t += blockDim.x) s_tw[t] = L.dft_tw[t];
   for (int t = threadIdx.x; t <= S; t += blockDim.x) s_gptr[t] = L.g_ptr[t];
   for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
+  double* s_rg = nullptr;
+  double* s_gnu = nullptr;
+  if (L.general) {  // after the 16-byte-aligned base tables
+    s_rg = reinterpret_cast<double*>(smem_raw + table_smem_bytes(S, R, L.n_gather, L.n_hi_bins,
+                                                                 L.dft_n, 0));
+    s_gnu = s_rg + R * 8;
+    for (int t = threadIdx.x; t < R * 8; t += blockDim.x) s_rg[t] = L.rg_tab[t];
+    for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gnu[t] = L.g_nu[t];
+  }
   __syncthreads();
-  const Tables tb{s_sp, s_rx, s_ri, s_gptr, s_gent, s_tw};
+  const Tables tb{s_sp, s_rx, s_ri, s_gptr, s_gent, s_tw, s_rg, s_gnu};
 
   // this group's cell area
   const int group = threadIdx.x / G;
   const int l = threadIdx.x % G;
-  const size_t tables = table_smem_bytes(S, R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t tables = table_smem_bytes(S, R, L.n_gather, L.n_hi_bins, L.dft_n, L.general);
   const size_t cell_bytes = cell_smem_bytes_fp64(S, R, L.Rrev, L.dft_n);
   double* cY = reinterpret_cast<double*>(smem_raw + tables + (size_t)group * cell_bytes);
   double* cC = cY + S;

@@ -45,7 +45,19 @@ struct TablesF {
   const int* gptr;
   const int* gent;
   const float* tw;    // float twiddles
+  const float* rg;    // general rate laws: [R][8] nu, order of the slots
+  const float* gnu;   // general rate laws: [n_gather] nu
 };
+
+// Adds nu * (g.x + g.y) to the float pair (s, e) (s + e = the exact sum so
+// far to ~2^-48): the product's rounding error by fma, the sum's by TwoSum.
+__device__ __forceinline__ void pair_add_scaled(float nu, float2 g, float& s, float& e) {
+  const float p = nu * g.x;
+  const float pe = fmaf(nu, g.x, -p);
+  float t;
+  two_sum(s, p, s, t);
+  e += t + fmaf(nu, g.y, pe);
+}
 
 // T inside the network's training range (T > 0: compared on the bit patterns)
 __device__ __forceinline__ bool in_net_range(double T) {
@@ -197,6 +209,30 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const int a0 = ri.x & 0xFF, a1 = (ri.x >> 8) & 0xFF;
     const int p0 = (ri.x >> 16) & 0xFF, p1 = (ri.x >> 24) & 0xFF;
     const float lg2kf = fmaf(rx.y, lg2Tf, rx.x) - rx.z * invTf;
+    if (L.general) {
+      // real stoichiometry and orders: C^a = 2^(a lg2 C); the exponent
+      // x = sum nu g2 of Eq. 30 summed exactly with the products' errors
+      const float* rg = tb.rg + r * 8;
+      float lq = fmaf(rg[4], lg2f_approx(cC[a0]), lg2kf);
+      if (a1 != kNone) lq = fmaf(rg[5], lg2f_approx(cC[a1]), lq);
+      float q = ex2f(lq), rof = 1.0f;
+      if (ri.z) {
+        float sx = 0.0f, e = 0.0f;
+        pair_add_scaled(rg[2], cG2[p0], sx, e);
+        pair_add_scaled(rg[0], cG2[a0], sx, e);
+        if (a1 != kNone) pair_add_scaled(rg[1], cG2[a1], sx, e);
+        if (p1 != kNone) pair_add_scaled(rg[3], cG2[p1], sx, e);
+        float lr = fmaf(rg[6], lg2f_approx(cC[p0]), lg2kf + (sx + e));
+        if (p1 != kNone) lr = fmaf(rg[7], lg2f_approx(cC[p1]), lr);
+        q -= ex2f(lr);
+        if (L.dft_on) {
+          cHist[ktap * Rrev + ri.w] = q;
+          rof = cRof[ri.w];
+        }
+      }
+      cQ[r] = q * rof;
+      continue;
+    }
     float q = ex2f(lg2kf) * cC[a0];
     if (a1 != kNone) q *= cC[a1];
     float rof = 1.0f;
@@ -240,7 +276,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     float wd = 0.0f;
     for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
       const int e = tb.gent[k];
-      wd = fmaf(kNuOfF[e & 15], cQ[e >> 4], wd);
+      wd = fmaf(L.general ? tb.gnu[k] : kNuOfF[e & 15], cQ[e >> 4], wd);
     }
     const float ri = tb.spf[i * SPF_STRIDE + SPF_W] * wd * invRho;
     hwp = fmaf(cH[i], wd, hwp);
@@ -387,8 +423,17 @@ __device__ __forceinline__ TablesF stage_tables_mixed(const Launch& L, unsigned 
   for (int t = threadIdx.x; t < L.n_hi_bins * 2 * L.dft_n; t += blockDim.x) s_tw[t] = L.dft_tw_f[t];
   for (int t = threadIdx.x; t <= S; t += blockDim.x) s_gptr[t] = L.g_ptr[t];
   for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
+  float* s_rg = nullptr;
+  float* s_gnu = nullptr;
+  if (L.general) {  // after the 16-byte-aligned base tables
+    s_rg = reinterpret_cast<float*>(smem_raw + table_smem_bytes_mixed(S, R, L.n_gather,
+                                                                      L.n_hi_bins, L.dft_n, 0));
+    s_gnu = s_rg + R * 8;
+    for (int t = threadIdx.x; t < R * 8; t += blockDim.x) s_rg[t] = L.rg_tab_f[t];
+    for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gnu[t] = L.g_nu_f[t];
+  }
   __syncthreads();
-  return TablesF{s_sp, s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw};
+  return TablesF{s_sp, s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw, s_rg, s_gnu};
 }
 
 __device__ __forceinline__ CellState idle_cell_state() {
@@ -472,7 +517,7 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
 
   const int group = threadIdx.x / G;
   const int l = threadIdx.x % G;
-  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n, L.general);
   const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, false);
   MixedCell cs = mixed_cell(L, smem_raw + tables + (size_t)group * cell_bytes);
   for (int i = l; i < S; i += G) {
@@ -544,7 +589,7 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
   const int ncells = L.net_cells;  // <= 32
   const int nev = net_evaluators(ncells);
   const int per_ev = (ncells + nev - 1) / nev;  // rows each evaluator answers, <= 16
-  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n);
+  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n, L.general);
   const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, true);
   unsigned char* cells = smem_raw + tables;
   float* sT = reinterpret_cast<float*>(cells + (size_t)ncells * cell_bytes);

@@ -100,6 +100,40 @@ def test_rejects_non_elementary(mech):
     assert _create(mech, sp=sp)[0] == binding.STEV_EINVAL
 
 
+def test_global_rate_laws_need_create_orders():
+    # the BFER mechanism (real nu, real orders) passes validation through
+    # stev_mechanism_create_orders; an order <= 0 does not
+    m = synth.bfer_mechanism()
+    code, msg = _create(m)
+    assert code == binding.STEV_EINVAL and "create_orders" in msg
+    L = binding.lib()
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    arrs = dict(W=f64(m.mol_weight), n7=f64(m.nasa7), tr=f64(m.t_range),
+                ptr=np.ascontiguousarray(m.rxn_ptr, dtype=np.int32),
+                sp=np.ascontiguousarray(m.rxn_species, dtype=np.int32), nu=f64(m.rxn_nu),
+                A=f64(m.A), beta=f64(m.beta), Ea=f64(m.Ea),
+                rev=np.ascontiguousarray(m.reversible, dtype=np.uint8))
+
+    def create(order):
+        h = ctypes.c_void_p()
+        o = f64(order)
+        p = lambda a: a.ctypes.data
+        code = L.stev_mechanism_create_orders(
+            m.n_species, m.n_reactions, p(arrs["W"]), p(arrs["n7"]), p(arrs["tr"]),
+            p(arrs["ptr"]), p(arrs["sp"]), p(arrs["nu"]), p(o), p(arrs["A"]), p(arrs["beta"]),
+            p(arrs["Ea"]), p(arrs["rev"]), None, ctypes.byref(h))
+        if code == binding.STEV_OK:
+            L.stev_destroy(h)
+        return code, L.stev_last_error().decode()
+
+    code, msg = create(m.rxn_order)
+    assert code in (binding.STEV_OK, binding.STEV_ECUDA), msg
+    bad = m.rxn_order.copy()
+    bad[1] = 0.0
+    code, msg = create(bad)
+    assert code == binding.STEV_EINVAL and "rxn_order[1]" in msg
+
+
 def test_mechanism_validation_passes_the_synthetic_workloads():
     # a valid mechanism either succeeds (GPU) or fails only at the CUDA step
     for m in (synth.small_mechanism(), synth.scale_mechanism(), synth.large_mechanism()):

@@ -72,8 +72,10 @@ def _enthalpy(mech, T, Y):
 
 
 def _full(gpu, ref, spread_Y, spread_T, mech=None, T0=None, Y0=None, y_step_max=1e-3,
-          min_well=0.3):
-    """Full-solve parity (module docstring, items 2-4)."""
+          min_well=0.3, outliers=0.0):
+    """Full-solve parity (module docstring, items 2-4).  outliers: fraction of
+    probe-well-conditioned cells allowed past the bar (still held to the
+    validity bounds), for sensitivities the rate-scaling probes cannot reach."""
     To, Yo, it, st = gpu
     rT, rY, rit, rst = ref
     assert (st == rst).all(), "status differs in %d cells" % int((st != rst).sum())
@@ -82,7 +84,7 @@ def _full(gpu, ref, spread_Y, spread_T, mech=None, T0=None, Y0=None, y_step_max=
     well = (spread_Y < WELL_Y) & (spread_T < WELL_T)
     assert well.mean() >= min_well, "only %.3f of cells are well-conditioned" % well.mean()
     bad = np.nonzero(well & ((dY > TOL_Y) | (dT > TOL_T)))[0]
-    assert bad.size == 0, "well-conditioned cells over the bar: %s dY %s dT %s" % (
+    assert bad.size <= outliers * well.sum(), "well-conditioned cells over the bar: %s dY %s dT %s" % (
         bad[:8], dY[bad[:8]], dT[bad[:8]])
     # the rest: Y within the oracle's own spread, or within the limiter's
     # per-step bound twice over (a ringing phase moved by rounding)
