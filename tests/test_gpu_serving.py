@@ -207,3 +207,30 @@ def test_serving_prefix_against_oracle():
     srv.close()
     for m in ms:
         m.close()
+
+
+def test_global_rate_laws_in_the_mix():
+    # the BFER mechanism (real orders, real stoichiometry) served beside the
+    # 8/20 mechanism: each request's results equal its solve alone
+    tabs = [synth.bfer_mechanism(), synth.small_mechanism()]
+    ms = [Mechanism(t) for t in tabs]
+    reqs = []
+    for k in range(6):
+        mi = k % 2
+        n = [700, 1500, 300][k // 2]
+        if mi == 0:
+            T, P, Y = synth.bfer_cells(tabs[0], n, seed=20 + k)
+        else:
+            T, P, Y = synth.make_cells(tabs[1], n, seed=20 + k)
+        reqs.append((mi, T, P, Y, 1e-3))
+    alone = [ms[mi].solve_host(T, P, Y, dt) for mi, T, P, Y, dt in reqs]
+    srv = Server(ms, sm_share=[60, 60], mem_budget=64 << 20)
+    ids = [srv.submit(mi, T, P, Y, dt) for mi, T, P, Y, dt in reqs]
+    got = _drain(srv, len(ids))
+    for rid, ref in zip(ids, alone):
+        assert got[rid]["status"] == 0
+        for a, b in zip(got[rid]["out"], ref):
+            np.testing.assert_array_equal(a, b)
+    srv.close()
+    for m in ms:
+        m.close()
