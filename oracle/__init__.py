@@ -74,6 +74,10 @@ PROBES = {"kf_up": ["-DORACLE_KF_SCALE=(1.0+2.220446049250313e-16)"],
           # concentrations or net rates rounded to float every step
           "round32_C": ["-DORACLE_ROUND32_C"],
           "round32_q": ["-DORACLE_ROUND32_Q"],
+          # every reverse term times (1 + 2^-22 xi), xi a hash in [-1, 1): no
+          # equilibrium cancels exactly (two seeds)
+          "qnoise32_a": ["-DORACLE_Q_NOISE=2.384185791015625e-07", "-DORACLE_Q_NOISE_SEED=1"],
+          "qnoise32_b": ["-DORACLE_Q_NOISE=2.384185791015625e-07", "-DORACLE_Q_NOISE_SEED=2"],
           # real-order powers C^a (global rate laws) changed by 4 ulp (math
           # libraries' pow differ by a few ulp), or by 2^-17 (a single-precision
           # 2^(a lg2 C) with |a lg2 C| up to ~32)
@@ -83,7 +87,7 @@ PROBES = {"kf_up": ["-DORACLE_KF_SCALE=(1.0+2.220446049250313e-16)"],
           "pow32_down": ["-DORACLE_POW_SCALE=(1.0-7.62939453125e-06)"]}
 PROBE_LEVELS = {"fp64": ("kf_up", "kf_down", "K_up", "K_down"),
                 "fp32": ("kf32_up", "kf32_down", "K32_up", "K32_down", "round32_C",
-                         "round32_q")}
+                         "round32_q", "qnoise32_a", "qnoise32_b")}
 # probes that only matter for mechanisms with real reaction orders
 POW_PROBES = {"fp64": ("pow_up", "pow_down"), "fp32": ("pow32_up", "pow32_down")}
 # single-precision-sized changes of the thresholds that take discrete
@@ -274,7 +278,9 @@ def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] =
     probe builds of the given level: "fp64" changes every kf by one ulp and
     every K by 64 ulp; "fp32" by 2^-22 and 2^-18, the size of the rounding
     of a single-precision rate and of its exponent, rounds every
-    concentration or every net rate to float, and moves the limiter's
+    concentration or every net rate to float, perturbs every reverse term by
+    a hashed relative 2^-22 (so that no equilibrium cancels exactly, as none
+    does with FP32 rates), and moves the limiter's
     Y_step^max and the ringing tolerances by 2^-22; for mechanisms with real
     reaction orders also every power C^a by 4 ulp ("fp64") or 2^-17
     ("fp32").  A cell whose spread is far below a tolerance is

@@ -65,6 +65,37 @@
 #else
 #define ORACLE_C(x) (x)
 #endif
+/* Single-precision noise probe (ORACLE_Q_NOISE = a): every reverse term of
+ * a net rate times (1 + a xi), xi in [-1, 1) from a hash (the splitmix64
+ * finaliser) of the cell's rate-evaluation count, the reaction index and
+ * ORACLE_Q_NOISE_SEED, so that no equilibrium cancels exactly, as none does
+ * with FP32 rates.  The uniform scalings above move an exact fixed point
+ * without making it inexact, so they cannot show a cell whose stability
+ * rests on exact cancellation. */
+#ifdef ORACLE_Q_NOISE
+#include <stdint.h>
+#ifndef ORACLE_Q_NOISE_SEED
+#define ORACLE_Q_NOISE_SEED 1
+#endif
+static _Thread_local uint64_t oracle_noise_calls;  /* reset per cell solve */
+static double oracle_noise(int r) {
+  uint64_t x = oracle_noise_calls * 0xD1B54A32D192ED03ULL;
+  x ^= (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ULL + (uint64_t)ORACLE_Q_NOISE_SEED;
+  x ^= x >> 30;
+  x *= 0xBF58476D1CE4E5B9ULL;
+  x ^= x >> 27;
+  x *= 0x94D049BB133111EBULL;
+  x ^= x >> 31;
+  return (double)(x >> 11) * 0x1p-52 - 1.0;
+}
+#define ORACLE_REV(x, r) ((x) * (1.0 + ORACLE_Q_NOISE * oracle_noise(r)))
+#define ORACLE_NOISE_NEXT() (++oracle_noise_calls)
+#define ORACLE_NOISE_RESET() (oracle_noise_calls = 0)
+#else
+#define ORACLE_REV(x, r) (x)
+#define ORACLE_NOISE_NEXT() ((void)0)
+#define ORACLE_NOISE_RESET() ((void)0)
+#endif
 #ifdef ORACLE_ROUND32_Q
 #define ORACLE_Q(x) ((double)(float)(x))
 #else
@@ -151,6 +182,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
   double *sR = malloc(sizeof(double) * S), *C = malloc(sizeof(double) * S);
   double *w = malloc(sizeof(double) * S), *q = malloc(sizeof(double) * R);
 
+  ORACLE_NOISE_NEXT();
   /* mixture molar mass and ideal-gas density */
   double inv_wbar = 0.0;
   for (int i = 0; i < S; ++i) inv_wbar += Y[i] / m->mol_weight[i];
@@ -190,7 +222,7 @@ void oracle_rates(const oracle_mech *m, const oracle_opts *o, double T, double P
         if (nu > 0.0) rev *= int_power(C[m->rxn_species[k]], entry_order(m, k));
       }
     }
-    q[r] = ORACLE_Q(fwd - rev);
+    q[r] = ORACLE_Q(fwd - ORACLE_REV(rev, r));
   }
 
   /* Eq. 14 effective rates, production rates in ascending reaction order */
@@ -282,6 +314,7 @@ int oracle_solve_cell_trace(const oracle_mech *m, const oracle_opts *o, double T
   for (int r = 0; r < R; ++r) rOF[r] = 1.0;                 /* Eq. 11 */
   double T = T0, t_rem = dt, dTdt = 0.0;
   long nhist = 0;
+  ORACLE_NOISE_RESET();
   int it = 0, status = ORACLE_CELL_OK;
   for (;;) {
     oracle_rates(m, o, T, P, Y, rOF, qraw, NULL, dYdt, &dTdt);
