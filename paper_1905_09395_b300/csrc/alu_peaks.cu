@@ -77,6 +77,25 @@ struct FTanh {
 };
 struct FRcp { static __device__ __forceinline__ float apply(float a, float b, float c) { return __frcp_rn(a) + c; } };
 
+// The DFMA probe with only the first `active` lanes of each warp working (the
+// others skip the loop): whether the FP64 pipe's time per warp instruction
+// depends on how many lanes it carries.
+__global__ void dfma_masked(double seed, double b, double c, int iters, int active, double* out) {
+  double a[CHAINS];
+#pragma unroll
+  for (int k = 0; k < CHAINS; ++k) a[k] = seed + (double)(threadIdx.x * 1e-7) + (double)(k * 1e-3);
+  if ((int)(threadIdx.x & 31) < active) {
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < CHAINS; ++k) a[k] = fma(a[k], b, c);
+    }
+  }
+  double s = a[0];
+#pragma unroll
+  for (int k = 1; k < CHAINS; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // One dependent chain in one warp per SM: latency per instruction.
 __global__ void dfma_latency(double seed, double b, double c, int iters, double* out, ClockRec* clk) {
   unsigned long long c0 = clock64();
@@ -140,6 +159,31 @@ int main() {
   run<FEx2, float>("ex2_approx", "mufu", 0.5f, 0.0f, 0.0f, 16384, sms, false);
   run<FTanh, float>("tanh_approx", "mufu", 0.5f, 0.0f, 0.0f, 16384, sms, false);
   run<FRcp, float>("frcp_rn", "fp32 (rcp routine)", 1.5f, 0.0f, 0.5f, 16384, sms, false);
+  {
+    const int block = 256, grid = sms * 8, iters = 4096;
+    double* out;
+    check(cudaMalloc(&out, sizeof(double) * grid * block), "malloc");
+    cudaEvent_t e0, e1; cudaEventCreate(&e0); cudaEventCreate(&e1);
+    printf("  \"dfma_masked_warp_instr_per_sm_per_clk_at_1919mhz\": {");
+    const int lanes[] = {32, 16, 8, 4, 1};
+    for (int li = 0; li < 5; ++li) {
+      dfma_masked<<<grid, block>>>(1.0, 0.9999999, 1e-9, iters / 10, lanes[li], out);
+      check(cudaDeviceSynchronize(), "masked warmup");
+      float best = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0);
+        dfma_masked<<<grid, block>>>(1.0, 0.9999999, 1e-9, iters, lanes[li], out);
+        cudaEventRecord(e1);
+        check(cudaEventSynchronize(e1), "masked");
+        float ms; cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+      }
+      const double warp_instr = (double)grid * (block / 32) * CHAINS * iters;
+      printf("\"%d\": %.4f%s", lanes[li], warp_instr / (best * 1e-3) / (sms * 1919e6),
+             li < 4 ? ", " : "},\n");
+    }
+    cudaFree(out); cudaEventDestroy(e0); cudaEventDestroy(e1);
+  }
   {
     double* out; ClockRec* clk;
     check(cudaMalloc(&out, sizeof(double) * sms * 32), "malloc");

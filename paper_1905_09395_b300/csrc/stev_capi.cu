@@ -59,6 +59,7 @@ struct stev_mechanism {
   double* d_sp = nullptr;
   double* d_rx = nullptr;
   int4* d_ri = nullptr;
+  int4* d_rim = nullptr;  // the mixed kernels' copy (unused slot = S)
   int* d_gptr = nullptr;
   int* d_gent = nullptr;
   double* d_tw = nullptr;
@@ -140,7 +141,7 @@ static stev_status check_options(const stev_options* o) {
 }
 
 static void free_mech(stev_mechanism* m) {
-  void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
+  void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_rim, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
                   m->d_twf, m->d_counter, m->d_mlp_params, m->d_mlp_W2, m->d_mlp_W3, m->d_mlp_misc,
                   m->d_bdesc, m->d_boff, m->d_net_stalls, m->d_rg, m->d_gnu, m->d_rgf, m->d_gnuf,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
@@ -151,13 +152,16 @@ static void free_mech(stev_mechanism* m) {
 
 typedef void (*KernelFn)(Launch);
 
-static KernelFn select_kernel(int precision, int G, int thermo = STEV_THERMO_POLY) {
+// The mixed kernels come with the DFT window fixed at the paper's N = 13
+// (taps unrolled) and for any other N.
+static KernelFn select_kernel(int precision, int G, int thermo, int dft_n) {
   if (precision == STEV_MIXED) {
-    if (thermo != STEV_THERMO_POLY) return stev_mixed_net_kernel;
+    const bool n13 = dft_n == 13;
+    if (thermo != STEV_THERMO_POLY) return n13 ? stev_mixed_net_kernel<13> : stev_mixed_net_kernel<0>;
     switch (G) {
-      case 8: return stev_mixed_kernel<8>;
-      case 16: return stev_mixed_kernel<16>;
-      default: return stev_mixed_kernel<32>;
+      case 8: return n13 ? stev_mixed_kernel<8, 13> : stev_mixed_kernel<8, 0>;
+      case 16: return n13 ? stev_mixed_kernel<16, 13> : stev_mixed_kernel<16, 0>;
+      default: return n13 ? stev_mixed_kernel<32, 13> : stev_mixed_kernel<32, 0>;
     }
   }
   switch (G) {
@@ -207,7 +211,7 @@ static stev_status configure(stev_mechanism* m) {
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
   const size_t smem = tables + (size_t)cells * cell + (net ? net_cta_smem_bytes(cells) : 0);
   const int block = cells * G + (net ? 32 * net_evaluators(cells) : 0);
-  KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo);
+  KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo, m->opt.dft_n);
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
@@ -406,22 +410,47 @@ extern "C" stev_status stev_mechanism_create_orders(
   TRY_OR_FREE(upload((void**)&m->d_sp, sp.data(), sp.size() * sizeof(double)));
   TRY_OR_FREE(upload((void**)&m->d_rx, rx.data(), rx.size() * sizeof(double)));
   TRY_OR_FREE(upload((void**)&m->d_ri, ri.data(), ri.size() * sizeof(int4)));
+  std::vector<int4> rim(ri);
+  for (int4& v : rim) {
+    int x = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int sl = (v.x >> (8 * k)) & 0xFF;
+      x |= (sl == kNone ? S : sl) << (8 * k);
+    }
+    v.x = x;
+  }
+  TRY_OR_FREE(upload((void**)&m->d_rim, rim.data(), rim.size() * sizeof(int4)));
   TRY_OR_FREE(upload((void**)&m->d_tw, tw.data(), tw.size() * sizeof(double)));
-  // float tables of the mixed kernel (log2 space for the MUFU exponentials)
-  std::vector<float> spf((size_t)S * SPF_STRIDE, 0.0f);
+  // float tables of the mixed kernel (log2 space for the MUFU exponentials),
+  // coefficient-major: row k of species i at [k * S + i]
+  std::vector<float> spf((size_t)SF_ROWS * S, 0.0f);
+  auto put = [&](int row, int i, double v) { spf[(size_t)row * S + i] = (float)v; };
+  auto put_pair = [&](int row, int i, double v) {  // hi row, then lo row
+    const float h = (float)v;
+    spf[(size_t)row * S + i] = h;
+    spf[(size_t)(row + 1) * S + i] = (float)(v - (double)h);
+  };
+  const double ln_pref = std::log(kPatm / kRu);
   for (int i = 0; i < S; ++i) {
     const double* e = &sp[(size_t)i * SP_STRIDE];
-    float* f = &spf[(size_t)i * SPF_STRIDE];
-    f[SPF_W] = (float)e[SP_W];
-    f[SPF_INVW] = (float)e[SP_INVW];
+    put(SF_W, i, e[SP_W]);
+    put(SF_INVW, i, e[SP_INVW]);
+    put_pair(SF_SPLIT_H, i, e[SP_TSPLIT]);
     for (int rg = 0; rg < 2; ++rg) {
       const double* b = e + (rg == 0 ? SP_LOW : SP_HIGH);
-      float* bf = f + (rg == 0 ? SPF_LOW : SPF_HIGH);
-      for (int k = 0; k < 6; ++k) bf[BF_A0 + k] = (float)b[B_A0 + k];
-      bf[BF_H1] = (float)b[B_H1];
-      bf[BF_H2] = (float)b[B_H2];
-      bf[BF_H3] = (float)b[B_H3];
-      bf[BF_H4] = (float)b[B_H4];
+      const int fb = rg == 0 ? SF_LOW : SF_HIGH;
+      for (int k = 0; k < 6; ++k) put(fb + BF_A0 + k, i, b[B_A0 + k]);
+      put(fb + BF_H1, i, b[B_H1]);
+      put(fb + BF_H2, i, b[B_H2]);
+      put(fb + BF_H3, i, b[B_H3]);
+      put(fb + BF_H4, i, b[B_H4]);
+      // g2 = log2 e (G/RT - ln(P_atm/R_u) + ln T) over the basis
+      // 1, ln T, 1/T, T, T^2, T^3, T^4 (G/RT of Eq. 16's NASA-7 form)
+      const double c[7] = {kLog2e * (b[B_A0] - b[B_A6] - ln_pref), kLog2e * (1.0 - b[B_A0]),
+                           kLog2e * b[B_A5], -kLog2e * b[B_H1], -kLog2e * b[B_G2],
+                           -kLog2e * b[B_G3], -kLog2e * b[B_G4]};
+      const int gb = rg == 0 ? SF_GLOW : SF_GHIGH;
+      for (int k = 0; k < 7; ++k) put_pair(gb + 2 * k, i, c[k]);
     }
   }
   std::vector<float4> rxf(R);
@@ -507,6 +536,7 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   L.sp_tab = m->d_sp;
   L.rx_tab = m->d_rx;
   L.rx_idx = m->d_ri;
+  L.rx_idx_m = m->d_rim;
   L.g_ptr = m->d_gptr;
   L.g_ent = m->d_gent;
   L.dft_tw = m->d_tw;
@@ -567,7 +597,7 @@ static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, co
 
 static stev_status launch_persistent(stev_mechanism* m, const Launch& L, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned long long), s));
-  select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<m->grid, m->block, m->smem, s>>>(L);
+  select_kernel(m->opt.precision, m->G, m->opt.thermo, m->opt.dft_n)<<<m->grid, m->block, m->smem, s>>>(L);
   CUDA_TRY(cudaGetLastError());
   return STEV_OK;
 }
@@ -716,7 +746,7 @@ stev_status serve_launch(stev_mechanism* m, ServeCtl* ctl, ServeSlot* slots,
   L.serve_warps = grid * (m->cells * m->G / 32);  // warps holding cells
   L.y_soa = 0;
   CUDA_TRY(cudaMemsetAsync(&ctl->idle_warps, 0, 2 * sizeof(int), s));  // idle_warps, exiting
-  select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<grid, m->block, m->smem, s>>>(L);
+  select_kernel(m->opt.precision, m->G, m->opt.thermo, m->opt.dft_n)<<<grid, m->block, m->smem, s>>>(L);
   CUDA_TRY(cudaGetLastError());
   return STEV_OK;
 }
@@ -821,7 +851,7 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
   L.T_out = dTo; L.Y_out = dYo; L.iters = dit; L.status = dst;
   L.y_soa = 0;
   L.counter = counter;
-  select_kernel(m->opt.precision, m->G, m->opt.thermo)<<<m->grid, m->block, m->smem, s>>>(L);
+  select_kernel(m->opt.precision, m->G, m->opt.thermo, m->opt.dft_n)<<<m->grid, m->block, m->smem, s>>>(L);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(T_out, dTo, nn * 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(Y_out, dYo, nn * m->S * 8, cudaMemcpyDeviceToHost, s));

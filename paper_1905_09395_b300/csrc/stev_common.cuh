@@ -40,9 +40,11 @@ struct CellState {
   double T, P, t_rem;
   int it;
   int nhist;
-  double lnT;       // mixed kernel: ln T kept up to date incrementally
   double dt;        // this cell's fluid time step t_f
-  double hcap;      // mixed kernel: t_f * delta_max (Eq. 4's time cap)
+  double hcap;      // t_f * delta_max (Eq. 4's time cap)
+  // mixed kernels: T and ln T as float pairs (hi + lo, ~2^-48 relative), and
+  // the time cap as a float pair
+  float Th, Tl, lnTh, lnTl, hcap_h, hcap_l;
   long long lc;     // index inside its batch
   int b;            // its batch (batched launches)
 };

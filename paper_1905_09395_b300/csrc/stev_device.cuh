@@ -39,10 +39,17 @@ enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
        B_SIZE };
 enum { RX_LNA = 0, RX_BETA = 1, RX_EAR = 2, RX_DN = 3, RX_STRIDE = 4 };
-// float species table of the mixed kernel: W, 1/W, pad, pad, then per range
-// a0..a5 and the H/RT coefficients a1/2..a4/5
-enum { SPF_W = 0, SPF_INVW = 1, SPF_LOW = 4, SPF_HIGH = 14, SPF_STRIDE = 24 };
+// Float species table of the mixed kernels, coefficient-major ([row][S], so
+// that lane i reading species i walks consecutive banks): W, 1/W, T_split as
+// a float pair; per range a0..a5 and the H/RT coefficients a1/2..a4/5 (FP32);
+// per range the seven coefficients of the species' Gibbs term in log2 units,
+//   g2(T) = c0 + c1 lnT + c2/T + c3 T + c4 T^2 + c5 T^3 + c6 T^4
+//         = log2 e (G/RT - ln(P_atm/R_u) + lnT)         (Eq. 30's exponent),
+// each as a float pair (hi row, lo row) holding the FP64 value to ~2^-48.
+enum { SF_W = 0, SF_INVW = 1, SF_SPLIT_H = 2, SF_SPLIT_L = 3, SF_LOW = 4, SF_HIGH = 14,
+       SF_GLOW = 24, SF_GHIGH = 38, SF_ROWS = 52 };
 enum { BF_A0 = 0, BF_A1, BF_A2, BF_A3, BF_A4, BF_A5, BF_H1, BF_H2, BF_H3, BF_H4, BF_SIZE };
+enum { GF_SIZE = 14 };  // rows of one range's Gibbs block: c_k hi at 2k, lo at 2k + 1
 
 // gather entry: reaction index * 16 + (nu + 8); the stoichiometric factor is
 // read back from kNuOf[] so that no integer-to-double conversion is needed
@@ -75,10 +82,11 @@ struct Launch {
   const double* sp_tab;   // [S][SP_STRIDE]
   const double* rx_tab;   // [R][RX_STRIDE]
   const int4* rx_idx;     // [R]
+  const int4* rx_idx_m;   // [R] the same for the mixed kernels, an unused slot = S
   const int* g_ptr;       // [S+1] species-major gather lists
   const int* g_ent;       // [n_gather]
   const double* dft_tw;   // [n_hi_bins][2][dft_n]: cos, sin of -2 pi j m / N
-  const float* sp_tab_f;  // [S][SPF_STRIDE]        (mixed kernel)
+  const float* sp_tab_f;  // [SF_ROWS][S]           (mixed kernel)
   const float4* rx_tab_f; // [R] lg2 A, beta, Ea/R log2 e, dN (mixed kernel)
   const float* dft_tw_f;  // float twiddles          (mixed kernel)
   // general rate laws (real stoichiometry and orders, e.g. Eqs. 26-29): per
@@ -153,21 +161,22 @@ __host__ __device__ inline size_t cell_smem_bytes_fp64(int S, int R, int Rrev, i
 
 __host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gather, int n_hi_bins,
                                                          int dft_n, int general = 0) {
-  size_t b = (size_t)S * SP_STRIDE * 8 + (size_t)R * 16 + (size_t)R * 16 +
-             (size_t)S * SPF_STRIDE * 4 + (size_t)n_hi_bins * 2 * dft_n * 4 +
-             (size_t)(S + 1 + n_gather) * 4;
+  size_t b = (size_t)R * 16 + (size_t)R * 16 + (size_t)S * SF_ROWS * 4 +
+             (size_t)n_hi_bins * 2 * dft_n * 4 + (size_t)(S + 1 + n_gather) * 4;
   b = (b + 15) & ~(size_t)15;
   if (general) b += (size_t)R * 8 * 4 + (((size_t)n_gather * 4 + 15) & ~(size_t)15);
   return b;
 }
 
-// Mixed kernel cell: Y in FP64 and G/RT log2 e as a float pair (8 bytes each
-// per species); C, H/RT, a float copy of Y (S each), rates (R), history
-// [N][Rrev] and rOF (Rrev) in FP32; with the thermo network also the cell's
-// row of network outputs (2S rounded up to 8).
+// Mixed kernel cell: the Gibbs terms g2 as float pairs (S + 1: the last is
+// the unused-slot entry), Y as float pairs in two arrays (hi, lo), C (S + 1)
+// and H/RT (S), rates (R), history [Rrev][N | 1] and rOF (Rrev) in FP32; with
+// the thermo network also the cell's row of network outputs (2S rounded up
+// to 8).
 __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n,
                                                        bool mlp = false) {
-  size_t b = (size_t)16 * S + ((size_t)3 * S + R + (size_t)dft_n * Rrev + Rrev) * 4;
+  size_t b = (size_t)8 * (S + 1) +
+             ((size_t)4 * S + 1 + R + (size_t)(dft_n | 1) * Rrev + Rrev) * 4;
   if (mlp) b += (size_t)((2 * S + 7) / 8 * 8) * 4;
   return (b + 15) & ~(size_t)15;
 }

@@ -1,21 +1,30 @@
-// Mixed-precision STEV: rates in FP32, state update and Gibbs exponent in FP64.
+// Mixed-precision STEV: rates in FP32; state, ln T, 1/T and the Gibbs terms
+// of Eq. 30 in float-pair arithmetic on the FP32 pipe.
 //
 // Same structure as the FP64 kernel (a group of G lanes per cell, all cell
 // state in shared memory, species-major gather, ballot/popcount refill).
 // What changes is the arithmetic:
-//   FP64  Y and T (the forward Euler update of Eq. 18), t_rem and h, and G/RT
-//         of every species;
-//   FP64-grade, on the FP32 pipe: the per-reaction Gibbs difference
-//         dG/RT - dN ln(P_atm/RT) that sets K (Eq. 30).  It is where large
-//         terms cancel, so each species' FP64 value is split into an exact
-//         float pair hi + lo and the difference is summed with error-free
-//         transformations (Knuth's TwoSum), keeping >= 48 significant bits
-//         before the single rounding to FP32 that the exponential takes;
+//   float pairs (hi + lo, about 48 significant bits, built with error-free
+//         transformations: Knuth's TwoSum and FMA products): Y and T and
+//         their forward Euler update (Eq. 18); ln T (updated by ln(1 + dT/T)
+//         from its series, refreshed by the FP64 log every 256 steps) and 1/T;
+//         each species' Gibbs term of Eq. 30, a compensated dot product of its
+//         FP64 coefficients (split into float pairs on the host) with the
+//         float-pair basis 1, ln T, 1/T, T, T^2, T^3, T^4; and the per-reaction
+//         Gibbs difference dG/RT - dN ln(P_atm/RT) that sets K, summed from
+//         those pairs with TwoSum, so that the exponent keeps no cancellation
+//         loss before the single rounding to FP32 that the exponential takes
+//         (error ~1e-11 in log2 K, against ~1e-6 relative in the FP32 rates);
+//   FP64  t_rem and h (two instructions per step: which step ends at t_f is
+//         decided exactly as in the FP64 path);
 //   FP32  mixture, cp/R and H/RT (Eqs. 15-16), gamma and concentrations
 //         (Eqs. 6-7), forward and reverse rate constants (exponentials on the
 //         MUFU unit in base 2: k = 2^(log2 k)), rates of progress and rOF
 //         (Eq. 14), production rates, dT/dt, the limiter (Eqs. 1-5) and the
 //         ringing history and DFT test (Eqs. 8-13).
+// B300's FP64 pipe runs at 1/64 of the FP32 rate, and a warp's FP64
+// instruction costs it the same time whatever the number of active lanes, so
+// per-cell scalars in FP64 (one cell per warp) would cost 32 lanes' worth.
 #pragma once
 #include "stev_common.cuh"
 #include "stev_mlp.cuh"
@@ -37,9 +46,93 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) 
   err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// A float pair: the value h + l, |l| <= ulp(h).
+struct FF {
+  float h, l;
+};
+
+// Dekker's Fast2Sum: h + l == a + b exactly when |a| >= |b| (or a == 0).
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// s + e of any magnitudes as a float pair.
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+  FF r;
+  two_sum(s, e, r.h, r.l);
+  return r;
+}
+
+// x * y; the l * l term (2^-48 relative) is dropped.
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  return fast_two_sum(p, e);
+}
+
+// x + y
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  float s, t;
+  two_sum(x.h, y.h, s, t);
+  return fast_two_sum(s, t + (x.l + y.l));
+}
+
+// x + a * b for a float pair x, a float pair a and a float b (Eq. 18's update)
+__device__ __forceinline__ FF ff_add_mul(FF x, FF a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  float pe = fmaf(a.h, b, -p);
+  pe = fmaf(a.l, b, pe);
+  float s, t;
+  two_sum(x.h, p, s, t);
+  return fast_two_sum(s, t + (x.l + pe));
+}
+
+__device__ __forceinline__ FF ff_from_double(double x) {
+  const float h = (float)x;
+  return FF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(FF x) { return (double)x.h + (double)x.l; }
+
+// (s, e) += c * b for a float-pair coefficient (ch, cl) and a float-pair
+// basis value b: the product's rounding error by FMA, the sum's by TwoSum
+// (the compensated dot product of Ogita, Rump and Oishi, 2005, with float-pair
+// operands); s + e is the exact sum so far to ~2^-48 of the terms' magnitude.
+__device__ __forceinline__ void dot2_term(float ch, float cl, FF b, float& s, float& e) {
+  const float p = __fmul_rn(ch, b.h);
+  float pe = fmaf(ch, b.h, -p);
+  pe = fmaf(ch, b.l, pe);
+  pe = fmaf(cl, b.h, pe);
+  float t;
+  two_sum(s, p, s, t);
+  e += t + pe;
+}
+
+// ln(1 + u) for a float pair |u| <= 2^-7: u - u^2/2 + u^3 (1/3 - u/4 + u^2/5 -
+// u^3/6 + u^4/7), u^2 exact by FMA; the truncated terms are below 2^-59 and
+// the FP32 rounding of the u^3 part below 2^-46.
+__device__ __forceinline__ FF ff_log1p_small(FF u) {
+  const float q = __fmul_rn(u.h, u.h);
+  float qe = fmaf(u.h, u.h, -q);
+  qe = fmaf(2.0f * u.h, u.l, qe);
+  const float c3 =
+      q * u.h *
+      fmaf(fmaf(fmaf(fmaf(u.h, 0.142857149f, -0.166666672f), u.h, 0.2f), u.h, -0.25f), u.h,
+           0.333333343f);
+  float s, t;
+  two_sum(u.h, -0.5f * q, s, t);
+  return fast_two_sum(s, t + (u.l + fmaf(-0.5f, qe, c3)));
+}
+
+// T below the float pair (sh, sl) (both exact pairs)
+__device__ __forceinline__ bool ff_below(FF T, float sh, float sl) {
+  return T.h < sh || (T.h == sh && T.l < sl);
+}
+
 struct TablesF {
-  const double* sp;   // double species table (G/RT coefficients)
-  const float* spf;   // float species table
+  const float* spf;   // float species table [SF_ROWS][S]
   const float4* rxf;  // lg2 A, beta, Ea/R log2 e, dN
   const int4* ri;
   const int* gptr;
@@ -59,10 +152,10 @@ __device__ __forceinline__ void pair_add_scaled(float nu, float2 g, float& s, fl
   e += t + fmaf(nu, g.y, pe);
 }
 
-// T inside the network's training range (T > 0: compared on the bit patterns)
-__device__ __forceinline__ bool in_net_range(double T) {
-  const long long b = dbits(T);
-  return b >= dbits(kMlpTLow) && b <= dbits(kMlpTHigh);
+// T inside the network's training range (on the pair's high part; the same
+// test decides the request and its use)
+__device__ __forceinline__ bool in_net_range(float Th) {
+  return Th >= (float)kMlpTLow && Th <= (float)kMlpTHigh;
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -77,26 +170,17 @@ __device__ __forceinline__ float lg2f_approx(float x) {
   return r;
 }
 
-// ln(1+u) for |u| <= 2^-10 from its series to u^5 (truncation < 2^-60 |u|)
-__device__ __forceinline__ double log1p_small(double u) {
-  double c = fma(u, 0.2, -0.25);
-  c = fma(c, u, 1.0 / 3.0);
-  c = fma(c, u, -0.5);
-  c = fma(c, u, 1.0);
-  return c * u;
-}
-
 // The thermo network's outputs for a cell (MLP kernels): waits until the
 // evaluator has answered request net_tag (bounded; on a timeout the step
 // takes the polynomials and counts a stall), then adds Y cp/R / W to cpp
 // (and sets H/RT with L.mlp_h).  Returns the group's sum of cpp.
 template <int G>
-__device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, const float* cYf,
+__device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, const float* cYh,
                                             float* cH, const float* cTh,
                                             volatile int* net_ans, int net_tag,
-                                            bool use_net, double T, float Tf, float invTf, int l,
-                                            float cpp) {
+                                            bool use_net, FF T, float invTf, int l, float cpp) {
   const int S = L.S;
+  const float Tf = T.h;
   if (use_net) {
     bool answered = *net_ans == net_tag;
     if (!__all_sync(0xffffffffu, answered) && l == 0)
@@ -109,20 +193,22 @@ __device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, 
     __threadfence_block();
     if (answered) {
       for (int i = l; i < S; i += G) {
-        cpp = fmaf(cYf[i] * cTh[i], tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+        cpp = fmaf(cYh[i] * cTh[i], tb.spf[SF_INVW * S + i], cpp);
         if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
       }
     } else {
       if (l == 0) atomicAdd(L.net_stalls, 1ULL);
       for (int i = l; i < S; i += G) {
-        const float* b = tb.spf + i * SPF_STRIDE +
-                         (T < tb.sp[i * SP_STRIDE + SP_TSPLIT] ? SPF_LOW : SPF_HIGH);
-        const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf,
-                                    b[BF_A1]), Tf, b[BF_A0]);
-        cpp = fmaf(cYf[i] * cpR, tb.spf[i * SPF_STRIDE + SPF_INVW], cpp);
+        const float* f = tb.spf + i;
+        const bool lo = ff_below(T, f[SF_SPLIT_H * S], f[SF_SPLIT_L * S]);
+        const float* b = f + (lo ? SF_LOW : SF_HIGH) * S;
+        const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4 * S], Tf, b[BF_A3 * S]), Tf, b[BF_A2 * S]),
+                                    Tf, b[BF_A1 * S]), Tf, b[BF_A0 * S]);
+        cpp = fmaf(cYh[i] * cpR, f[SF_INVW * S], cpp);
         if (L.mlp_h) {
-          const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
-          cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+          const float hp = fmaf(fmaf(fmaf(b[BF_H4 * S], Tf, b[BF_H3 * S]), Tf, b[BF_H2 * S]), Tf,
+                                b[BF_H1 * S]);
+          cH[i] = fmaf(hp, Tf, b[BF_A0 * S]) + b[BF_A5 * S] * invTf;
         }
       }
     }
@@ -139,61 +225,77 @@ __device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, 
 // waits for that only where it first needs them: with H/RT from the network,
 // before the production rates; with cp/R only, before the temperature update,
 // after the damper (net_thermo).
-template <int G, bool MLP>
-__device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, double* cY,
-                                          float* cYf, float2* cG2, float* cC, float* cH,
+//
+// NT > 0: the DFT window N (Eq. 9) fixed at compile time (the taps unrolled);
+// NT = 0: N = L.dft_n.  The history is reaction-major, N taps of a reaction
+// contiguous at a stride of N rounded up to odd (lanes on consecutive
+// reactions hit distinct banks).  A missing reactant or product slot points
+// at species S, whose C is 1 and g2 is 0, so that products and Gibbs sums
+// need no branch.
+template <int G, bool MLP, int NT>
+__device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, float* cYh,
+                                          float* cYl, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
                                           CellState& st, const float* cTh,
                                           volatile int* net_ans, int net_tag) {
-  const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
-  const double T = st.T;
-  const bool use_net = MLP && in_net_range(T);  // one cell per warp
-  const double lnT = st.lnT;        // FP64: feeds G/RT
-  const float Tf = (float)T;
-  // 1/T in FP64: the FP32 reciprocal refined by two Newton steps (each squares
-  // the relative error: 2^-22 -> 2^-44 -> below the last bit)
-  double invT = (double)rcp_approx(Tf);
-  invT = fma(invT, fma(-T, invT, 1.0), invT);
-  invT = fma(invT, fma(-T, invT, 1.0), invT);
-  const float invTf = 1.0f / Tf;
+  const int S = L.S, R = L.R, Rrev = L.Rrev;
+  const int N = NT > 0 ? NT : L.dft_n;
+  const int NP = N | 1;
+  const FF T{st.Th, st.Tl};
+  const FF lnT{st.lnTh, st.lnTl};
+  const float Tf = T.h;
+  const bool use_net = MLP && in_net_range(Tf);  // one cell per warp
+  // 1/T: the FP32 reciprocal r, then 1/T = r / (1 - e), e = 1 - T r exact to
+  // ~2^-46 by FMA: lo = r (e + e^2)
+  const float r0 = rcp_approx(Tf);
+  float e0 = fmaf(-Tf, r0, 1.0f);
+  e0 = fmaf(-T.l, r0, e0);
+  const FF invT = fast_two_sum(r0, r0 * fmaf(e0, e0, e0));
+  const float invTf = invT.h;
   const float lg2Tf = lg2f_approx(Tf);
+  const FF T2 = ff_mul(T, T);
+  const FF T3 = ff_mul(T2, T);
+  const FF T4 = ff_mul(T2, T2);
 
   // mixture (FP32)
   float part = 0.0f;
-  for (int i = l; i < S; i += G) part = fmaf(cYf[i], tb.spf[i * SPF_STRIDE + SPF_INVW], part);
+  for (int i = l; i < S; i += G) part = fmaf(cYh[i], tb.spf[SF_INVW * S + i], part);
   const float sumYW = group_sum<G>(part);
   const float rho = Pf / ((float)kRu * Tf * sumYW);
 
-  // thermo: cp/R, H/RT in FP32; G/RT in FP64, in log2 units and with the
-  // standard-state pressure term of Eq. 30 folded in: g2 = (G/RT) log2 e -
-  // lg2(P_atm/RT), so that a reaction's sum of nu g2 is its whole exponent
-  // (sum nu = dN carries the pressure term)
-  const double lg2Pref = (L.ln_patm_over_ru - lnT) * kLog2e;
+  // thermo: cp/R, H/RT in FP32; the Gibbs term in log2 units with the
+  // standard-state pressure of Eq. 30 folded in, g2 = (G/RT - ln(P_atm/RT))
+  // log2 e, as a float pair (a reaction's sum of nu g2 is its whole exponent:
+  // sum nu = dN carries the pressure term)
   float cpp = 0.0f;
   for (int i = l; i < S; i += G) {
-    const float* spf = tb.spf + i * SPF_STRIDE;
-    const double* sp = tb.sp + i * SP_STRIDE;
-    const bool lo = T < sp[SP_TSPLIT];
-    const float* b = spf + (lo ? SPF_LOW : SPF_HIGH);
-    const double* bd = sp + (lo ? SP_LOW : SP_HIGH);
-    const float Yi = cYf[i];
+    const float* f = tb.spf + i;  // row k of species i at f[k * S]
+    const bool lo = ff_below(T, f[SF_SPLIT_H * S], f[SF_SPLIT_L * S]);
+    const float* b = f + (lo ? SF_LOW : SF_HIGH) * S;
+    const float* g = f + (lo ? SF_GLOW : SF_GHIGH) * S;
+    const float Yi = cYh[i];
     if (!use_net) {
-      const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4], Tf, b[BF_A3]), Tf, b[BF_A2]), Tf,
-                                  b[BF_A1]), Tf, b[BF_A0]);
-      cpp = fmaf(Yi * cpR, spf[SPF_INVW], cpp);
+      const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4 * S], Tf, b[BF_A3 * S]), Tf, b[BF_A2 * S]),
+                                  Tf, b[BF_A1 * S]), Tf, b[BF_A0 * S]);
+      cpp = fmaf(Yi * cpR, f[SF_INVW * S], cpp);
     }
     if (!(use_net && L.mlp_h)) {
-      const float hp = fmaf(fmaf(fmaf(b[BF_H4], Tf, b[BF_H3]), Tf, b[BF_H2]), Tf, b[BF_H1]);
-      cH[i] = fmaf(hp, Tf, b[BF_A0]) + b[BF_A5] * invTf;
+      const float hp = fmaf(fmaf(fmaf(b[BF_H4 * S], Tf, b[BF_H3 * S]), Tf, b[BF_H2 * S]), Tf,
+                            b[BF_H1 * S]);
+      cH[i] = fmaf(hp, Tf, b[BF_A0 * S]) + b[BF_A5 * S] * invTf;
     }
-    const double gp = fma(fma(fma(bd[B_G4], T, bd[B_G3]), T, bd[B_G2]), T, bd[B_H1]);
-    const double g2 =
-        fma(fma(bd[B_A0], 1.0 - lnT, fma(bd[B_A5], invT, -bd[B_A6])) - gp * T, kLog2e, -lg2Pref);
-    const float ghi = (float)g2;
-    cG2[i] = make_float2(ghi, (float)(g2 - (double)ghi));  // g2 == hi + lo to ~2^-48
+    float gs = g[0], ge = g[S];
+    dot2_term(g[2 * S], g[3 * S], lnT, gs, ge);
+    dot2_term(g[4 * S], g[5 * S], invT, gs, ge);
+    dot2_term(g[6 * S], g[7 * S], T, gs, ge);
+    dot2_term(g[8 * S], g[9 * S], T2, gs, ge);
+    dot2_term(g[10 * S], g[11 * S], T3, gs, ge);
+    dot2_term(g[12 * S], g[13 * S], T4, gs, ge);
+    const FF g2 = ff_norm(gs, ge);
+    cG2[i] = make_float2(g2.h, g2.l);
     const float y = fmaxf(Yi, 0.0f);
     const float ys = (L.alpha_f > 0.0f) ? y * __fdividef(y, L.alpha_f + y) : y;
-    cC[i] = rho * ys * spf[SPF_INVW];
+    cC[i] = rho * ys * f[SF_INVW * S];
   }
   float cpsum = 0.0f;
   if (!MLP) cpsum = group_sum<G>(cpp);
@@ -212,53 +314,45 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     if (L.general) {
       // real stoichiometry and orders: C^a = 2^(a lg2 C); the exponent
       // x = sum nu g2 of Eq. 30 summed exactly with the products' errors
+      // (an unused slot: species S, lg2 C = 0, order and nu 0)
       const float* rg = tb.rg + r * 8;
       float lq = fmaf(rg[4], lg2f_approx(cC[a0]), lg2kf);
-      if (a1 != kNone) lq = fmaf(rg[5], lg2f_approx(cC[a1]), lq);
+      lq = fmaf(rg[5], lg2f_approx(cC[a1]), lq);
       float q = ex2f(lq), rof = 1.0f;
       if (ri.z) {
         float sx = 0.0f, e = 0.0f;
         pair_add_scaled(rg[2], cG2[p0], sx, e);
         pair_add_scaled(rg[0], cG2[a0], sx, e);
-        if (a1 != kNone) pair_add_scaled(rg[1], cG2[a1], sx, e);
-        if (p1 != kNone) pair_add_scaled(rg[3], cG2[p1], sx, e);
+        pair_add_scaled(rg[1], cG2[a1], sx, e);
+        pair_add_scaled(rg[3], cG2[p1], sx, e);
         float lr = fmaf(rg[6], lg2f_approx(cC[p0]), lg2kf + (sx + e));
-        if (p1 != kNone) lr = fmaf(rg[7], lg2f_approx(cC[p1]), lr);
+        lr = fmaf(rg[7], lg2f_approx(cC[p1]), lr);
         q -= ex2f(lr);
         if (L.dft_on) {
-          cHist[ktap * Rrev + ri.w] = q;
+          cHist[ri.w * NP + ktap] = q;
           rof = cRof[ri.w];
         }
       }
       cQ[r] = q * rof;
       continue;
     }
-    float q = ex2f(lg2kf) * cC[a0];
-    if (a1 != kNone) q *= cC[a1];
+    float q = ex2f(lg2kf) * cC[a0] * cC[a1];
     float rof = 1.0f;
     if (ri.z) {
       // x = sum nu g2 as a float pair (s, e): TwoSum on the high parts,
       // plain sums of the error terms and low parts
-      const float2 gp0 = cG2[p0], ga0 = cG2[a0];
+      const float2 gp0 = cG2[p0], ga0 = cG2[a0], ga1 = cG2[a1], gp1 = cG2[p1];
       float sx, e, t;
       two_sum(gp0.x, -ga0.x, sx, t);
       e = t + (gp0.y - ga0.y);
-      if (a1 != kNone) {
-        const float2 g = cG2[a1];
-        two_sum(sx, -g.x, sx, t);
-        e += t - g.y;
-      }
-      if (p1 != kNone) {
-        const float2 g = cG2[p1];
-        two_sum(sx, g.x, sx, t);
-        e += t + g.y;
-      }
+      two_sum(sx, -ga1.x, sx, t);
+      e += t - ga1.y;
+      two_sum(sx, gp1.x, sx, t);
+      e += t + gp1.y;
       const float x = sx + e;
-      float rev = ex2f(lg2kf + x) * cC[p0];
-      if (p1 != kNone) rev *= cC[p1];
-      q -= rev;
+      q -= ex2f(lg2kf + x) * cC[p0] * cC[p1];
       if (L.dft_on) {
-        cHist[ktap * Rrev + ri.w] = q;
+        cHist[ri.w * NP + ktap] = q;
         rof = cRof[ri.w];
       }
     }
@@ -266,7 +360,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   }
   __syncwarp();
 
-  if (MLP && L.mlp_h) cpsum = net_thermo<G>(L, tb, cYf, cH, cTh, net_ans, net_tag, use_net, T, Tf,
+  if (MLP && L.mlp_h) cpsum = net_thermo<G>(L, tb, cYh, cH, cTh, net_ans, net_tag, use_net, T,
                                               invTf, l, cpp);
 
   // production rates, dY/dt, dT/dt terms and the limiter (FP32)
@@ -278,11 +372,11 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
       const int e = tb.gent[k];
       wd = fmaf(L.general ? tb.gnu[k] : kNuOfF[e & 15], cQ[e >> 4], wd);
     }
-    const float ri = tb.spf[i * SPF_STRIDE + SPF_W] * wd * invRho;
+    const float ri = tb.spf[SF_W * S + i] * wd * invRho;
     hwp = fmaf(cH[i], wd, hwp);
     cC[i] = ri;
     const float rstar = fmaxf(-ri, 1.0e-30f);
-    const float Yi = cYf[i];
+    const float Yi = cYh[i];
     const float ystar = (Yi < 1.0e-20f) ? 1.0f : 0.9f * Yi;
     tmin = fminf(tmin, __fdividef(fminf(L.y_step_max_f, ystar), rstar));
   }
@@ -290,12 +384,20 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   tmin = group_min<G>(tmin);
   float dTdt = 0.0f;
   if (!MLP) dTdt = -(Tf * hw) / (rho * cpsum);
-  // h = min(tmin, t_f delta_max), the last step ends at t_f; all >= 0, so the
-  // comparisons run on the bit patterns
+  // h = min(tmin, t_f delta_max), the last step ends at t_f: decided in FP64
+  // as in the FP64 path (all >= 0, so the comparisons run on the bit
+  // patterns); h as a float pair for the update
   const long long hb = min(dbits((double)tmin), dbits(st.hcap));
   const bool last = hb >= dbits(st.t_rem);
-  const double h = last ? st.t_rem : __longlong_as_double(hb);
-  const float hf = (float)h;
+  FF h;
+  if (last)
+    h = ff_from_double(st.t_rem);
+  else if (hb == dbits(st.hcap))
+    h = FF{st.hcap_h, st.hcap_l};
+  else
+    h = FF{tmin, 0.0f};
+  st.t_rem = last ? 0.0 : st.t_rem - __longlong_as_double(hb);
+  const float hf = h.h;
 
   // ringing detection and damping (Eqs. 8-13), FP32
   if (L.dft_on) {
@@ -303,35 +405,39 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
     const float tol_freq = L.tol_freq_f, tol_ring = L.tol_ring_f;
     const float r_fac = L.r_fac_f;
     for (int w = l; w < Rrev; w += G) {
-      const float x = cHist[ktap * Rrev + w] * hf;
-      cHist[ktap * Rrev + w] = x;
+      float* hw = cHist + w * NP;
+      const float x = hw[ktap] * hf;
+      hw[ktap] = x;
       float rof = cRof[w];
       if (full) {
-        float s = 0.0f;
-        for (int m = 0; m < N; ++m) s += cHist[m * Rrev + w];
+        // the window sum (storage order) and sum of |x| in one pass
+        float s = 0.0f, a = 0.0f;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          const float v = hw[m];
+          s += v;
+          a += fabsf(v);
+        }
         const float D0 = fabsf(s);
         float rstar = r_fac;
-        if (D0 < tol_freq) {
-          float a = 0.0f;
-          for (int m = 0; m < N; ++m) a += fabsf(cHist[m * Rrev + w]);
-          if (D0 < tol_ring * a) {
-            const float inv = 1.0f / a;
-            float max2 = 0.0f;
-            for (int bb = 0; bb < L.n_hi_bins; ++bb) {
-              const float* c = tb.tw + bb * 2 * N;
-              float re = 0.0f, im = 0.0f;
-              for (int m = 0; m < N; ++m) {
-                const float xm = cHist[m * Rrev + w];
-                re = fmaf(xm, c[m], re);
-                im = fmaf(xm, c[N + m], im);
-              }
-              re *= inv;
-              im *= inv;
-              max2 = fmaxf(max2, fmaf(re, re, im * im));
+        if (D0 < tol_freq && D0 < tol_ring * a) {
+          const float inv = 1.0f / a;
+          float max2 = 0.0f;
+          for (int bb = 0; bb < L.n_hi_bins; ++bb) {
+            const float* c = tb.tw + bb * 2 * N;
+            float re = 0.0f, im = 0.0f;
+#pragma unroll 1
+            for (int m = 0; m < N; ++m) {  // rare: not unrolled, taps reloaded
+              const float xm = hw[m];
+              re = fmaf(xm, c[m], re);
+              im = fmaf(xm, c[N + m], im);
             }
-            const float d = D0 * inv;
-            if (d * d < tol_ring * tol_ring * max2) rstar = L.inv_r_fac_f;
+            re *= inv;
+            im *= inv;
+            max2 = fmaxf(max2, fmaf(re, re, im * im));
           }
+          const float d = D0 * inv;
+          if (d * d < tol_ring * tol_ring * max2) rstar = L.inv_r_fac_f;
         }
         rof = fmaxf(fminf(rof * rstar, 1.0f), L.rof_min_f);
       } else {
@@ -345,35 +451,43 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
   if (MLP) {
     // cp/R only: its network answer is first needed here, which leaves the
     // evaluator the rates, the limiter and the damper to answer in
-    if (!L.mlp_h) cpsum = net_thermo<G>(L, tb, cYf, cH, cTh, net_ans, net_tag, use_net, T, Tf,
+    if (!L.mlp_h) cpsum = net_thermo<G>(L, tb, cYh, cH, cTh, net_ans, net_tag, use_net, T,
                                         invTf, l, cpp);
     dTdt = -(Tf * hw) / (rho * cpsum);
   }
 
-  // forward Euler in FP64 (Eq. 18)
+  // forward Euler (Eq. 18) in float pairs
   bool bad = false;
   for (int i = l; i < S; i += G) {
-    const double y = fma(h, (double)cC[i], cY[i]);
-    cY[i] = y;
-    cYf[i] = (float)y;
-    bad = bad || !isfinite(y);
+    const FF y = ff_add_mul(FF{cYh[i], cYl[i]}, h, cC[i]);
+    cYh[i] = y.h;
+    cYl[i] = y.l;
+    bad = bad || !isfinite(y.h);
   }
-  st.T = fma(h, (double)dTdt, T);
-  st.t_rem -= h;
+  const float pT = __fmul_rn(h.h, dTdt);
+  float peT = fmaf(h.h, dTdt, -pT);
+  peT = fmaf(h.l, dTdt, peT);
+  float sT, tT;
+  two_sum(T.h, pT, sT, tT);
+  const FF Tn = fast_two_sum(sT, tT + (T.l + peT));
+  st.Th = Tn.h;
+  st.Tl = Tn.l;
   st.it += 1;
-  // ln T for the next step: ln T' = ln T + ln(1 + u), u = (T' - T)/T, from the
-  // series while |u| <= 2^-10; the library log every 256 steps and on larger
-  // changes keeps the accumulated rounding below ~1e-13
-  const double u = (st.T - T) * invT;
-  if ((dbits(u) & 0x7FFFFFFFFFFFFFFFLL) <= dbits(0x1p-10) && (st.it & 255) != 0)
-    st.lnT = lnT + log1p_small(u);
+  // ln T for the next step: ln T' = ln T + ln(1 + u), u = (T' - T)/T =
+  // h dT/dt / T, from the series while |u| <= 2^-7; the FP64 log every 256
+  // steps and on larger changes keeps the accumulated rounding below ~1e-12
+  const FF u = ff_mul(FF{pT, peT}, invT);
+  FF lnTn;
+  if (fabsf(u.h) <= 0x1p-7f && (st.it & 255) != 0)
+    lnTn = ff_add(lnT, ff_log1p_small(u));
   else
-    st.lnT = log(st.T);
-  const long long Tb = dbits(st.T);
-  bad = group_any<G>(bad) || (Tb & 0x7FF0000000000000LL) == 0x7FF0000000000000LL;
+    lnTn = ff_from_double(log(ff_to_double(Tn)));
+  st.lnTh = lnTn.h;
+  st.lnTl = lnTn.l;
+  bad = group_any<G>(bad) || !isfinite(Tn.h);
   __syncwarp();
   if (bad) return 2;
-  if (Tb < dbits(200.0) || Tb > dbits(6000.0)) return 3;
+  if (ff_below(Tn, 200.0f, 0.0f) || Tn.h > 6000.0f || (Tn.h == 6000.0f && Tn.l > 0.0f)) return 3;
   if (last) return 0;
   if (st.it >= L.max_iters) return 1;
   return -1;
@@ -381,11 +495,11 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, do
 
 // Shared-memory pointers of one resident cell of the mixed kernels.
 struct MixedCell {
-  double* Y;
   float2* G2;
+  float* Yh;  // Y as float pairs: high parts (the FP32 view of Y) ...
+  float* Yl;  // ... and low parts
   float* C;
   float* H;
-  float* Yf;  // float shadow of Y for the FP32 parts
   float* Q;
   float* Hist;
   float* Rof;
@@ -394,32 +508,44 @@ struct MixedCell {
 
 __device__ __forceinline__ MixedCell mixed_cell(const Launch& L, unsigned char* base) {
   MixedCell c;
-  c.Y = reinterpret_cast<double*>(base);
-  c.G2 = reinterpret_cast<float2*>(c.Y + L.S);
-  c.C = reinterpret_cast<float*>(c.G2 + L.S);
-  c.H = c.C + L.S;
-  c.Yf = c.H + L.S;
-  c.Q = c.Yf + L.S;
-  c.Hist = c.Q + L.R;
-  c.Rof = c.Hist + L.dft_n * L.Rrev;
+  c.G2 = reinterpret_cast<float2*>(base);  // S + 1 (the unused-slot entry)
+  c.Yh = reinterpret_cast<float*>(c.G2 + L.S + 1);
+  c.Yl = c.Yh + L.S;
+  c.C = c.Yl + L.S;                        // S + 1
+  c.H = c.C + L.S + 1;
+  c.Q = c.H + L.S;
+  c.Hist = c.Q + L.R;                      // [Rrev][N | 1]
+  c.Rof = c.Hist + (L.dft_n | 1) * L.Rrev;
   c.Th = c.Rof + L.Rrev;
   return c;
+}
+
+// Zeroes a cell block's Y and sets the unused-slot entries (C = 1, g2 = 0).
+template <int G>
+__device__ __forceinline__ void init_mixed_cell(const Launch& L, const MixedCell& cs, int l) {
+  for (int i = l; i < L.S; i += G) {
+    cs.Yh[i] = 0.0f;
+    cs.Yl[i] = 0.0f;
+  }
+  if (l == 0) {
+    cs.C[L.S] = 1.0f;
+    cs.G2[L.S] = make_float2(0.0f, 0.0f);
+  }
+  __syncwarp();
 }
 
 // Stages the mechanism tables of the mixed kernels in shared memory.
 __device__ __forceinline__ TablesF stage_tables_mixed(const Launch& L, unsigned char* smem_raw) {
   const int S = L.S, R = L.R;
-  double* s_sp = reinterpret_cast<double*>(smem_raw);
-  float4* s_rxf = reinterpret_cast<float4*>(s_sp + S * SP_STRIDE);
+  float4* s_rxf = reinterpret_cast<float4*>(smem_raw);
   int4* s_ri = reinterpret_cast<int4*>(s_rxf + R);
   float* s_spf = reinterpret_cast<float*>(s_ri + R);
-  float* s_tw = s_spf + S * SPF_STRIDE;
+  float* s_tw = s_spf + S * SF_ROWS;
   int* s_gptr = reinterpret_cast<int*>(s_tw + L.n_hi_bins * 2 * L.dft_n);
   int* s_gent = s_gptr + S + 1;
-  for (int t = threadIdx.x; t < S * SP_STRIDE; t += blockDim.x) s_sp[t] = L.sp_tab[t];
   for (int t = threadIdx.x; t < R; t += blockDim.x) s_rxf[t] = L.rx_tab_f[t];
-  for (int t = threadIdx.x; t < R; t += blockDim.x) s_ri[t] = L.rx_idx[t];
-  for (int t = threadIdx.x; t < S * SPF_STRIDE; t += blockDim.x) s_spf[t] = L.sp_tab_f[t];
+  for (int t = threadIdx.x; t < R; t += blockDim.x) s_ri[t] = L.rx_idx_m[t];
+  for (int t = threadIdx.x; t < S * SF_ROWS; t += blockDim.x) s_spf[t] = L.sp_tab_f[t];
   for (int t = threadIdx.x; t < L.n_hi_bins * 2 * L.dft_n; t += blockDim.x) s_tw[t] = L.dft_tw_f[t];
   for (int t = threadIdx.x; t <= S; t += blockDim.x) s_gptr[t] = L.g_ptr[t];
   for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
@@ -433,7 +559,19 @@ __device__ __forceinline__ TablesF stage_tables_mixed(const Launch& L, unsigned 
     for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gnu[t] = L.g_nu_f[t];
   }
   __syncthreads();
-  return TablesF{s_sp, s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw, s_rg, s_gnu};
+  return TablesF{s_spf, s_rxf, s_ri, s_gptr, s_gent, s_tw, s_rg, s_gnu};
+}
+
+__device__ __forceinline__ void set_mixed_scalars(CellState& st) {
+  const FF T = ff_from_double(st.T);
+  const FF lnT = ff_from_double(log(st.T));
+  const FF hc = ff_from_double(st.hcap);
+  st.Th = T.h;
+  st.Tl = T.l;
+  st.lnTh = lnT.h;
+  st.lnTl = lnT.l;
+  st.hcap_h = hc.h;
+  st.hcap_l = hc.l;
 }
 
 __device__ __forceinline__ CellState idle_cell_state() {
@@ -448,7 +586,7 @@ __device__ __forceinline__ CellState idle_cell_state() {
   st.b = 0;
   st.it = 0;
   st.nhist = 0;
-  st.lnT = log(1000.0);
+  set_mixed_scalars(st);
   return st;
 }
 
@@ -477,13 +615,14 @@ __device__ __forceinline__ void load_mixed_cell(const Launch& L, long long c, in
   st.t_rem = io.dt;
   st.it = 0;
   st.nhist = 0;
-  st.lnT = log(st.T);
+  set_mixed_scalars(st);
   Pf = (float)st.P;
-  if (L.y_soa)
-    for (int i = l; i < S; i += G) cs.Y[i] = __ldcg(io.Y + (long long)i * io.n + lc);
-  else
-    for (int i = l; i < S; i += G) cs.Y[i] = __ldcg(io.Y + lc * S + i);
-  for (int i = l; i < S; i += G) cs.Yf[i] = (float)cs.Y[i];
+  for (int i = l; i < S; i += G) {
+    const double y = L.y_soa ? __ldcg(io.Y + (long long)i * io.n + lc) : __ldcg(io.Y + lc * S + i);
+    const FF yf = ff_from_double(y);
+    cs.Yh[i] = yf.h;
+    cs.Yl[i] = yf.l;
+  }
   for (int w = l; w < L.Rrev; w += G) cs.Rof[w] = 1.0f;
 }
 
@@ -495,21 +634,21 @@ __device__ __forceinline__ void store_mixed_cell(const Launch& L, int l, MixedCe
   const CellIO io = cell_io(L, st.b);
   const long long c = st.lc;
   if (l == 0) {
-    io.T_out[c] = st.T;
+    io.T_out[c] = ff_to_double(FF{st.Th, st.Tl});
     io.iters[c] = st.it;
     io.status[c] = (unsigned char)outcome;
   }
   if (L.y_soa)
-    for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = cs.Y[i];
+    for (int i = l; i < S; i += G) io.Y_out[(long long)i * io.n + c] = ff_to_double(FF{cs.Yh[i], cs.Yl[i]});
   else
-    for (int i = l; i < S; i += G) io.Y_out[c * S + i] = cs.Y[i];
+    for (int i = l; i < S; i += G) io.Y_out[c * S + i] = ff_to_double(FF{cs.Yh[i], cs.Yl[i]});
   if (L.serve) serve_cell_done<G>(L, st.b, io.n, l);
   st.cell = -1;
 }
 
 // Mixed-precision persistent kernel, NASA-7 thermo: lane groups of G lanes,
 // one cell each, refilled in place (Sec. 2.4).
-template <int G>
+template <int G, int NT>
 __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = L.S;
@@ -520,10 +659,7 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
   const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n, L.general);
   const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, false);
   MixedCell cs = mixed_cell(L, smem_raw + tables + (size_t)group * cell_bytes);
-  for (int i = l; i < S; i += G) {
-    cs.Y[i] = 0.0;
-    cs.Yf[i] = 0.0f;
-  }
+  init_mixed_cell<G>(L, cs, l);
 
   const unsigned long long n = (unsigned long long)L.n_cells;
   CellState st = idle_cell_state();
@@ -559,7 +695,7 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
     }
     idle_since = 0;
     idle_sleep = 1000u;
-    const int outcome = step_mixed<G, false>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
+    const int outcome = step_mixed<G, false, NT>(L, tb, cs.Yh, cs.Yl, cs.G2, cs.C, cs.H, cs.Q,
                                              cs.Hist, cs.Rof, Pf, l, st, nullptr, nullptr, 0);
     if (st.cell >= 0 && outcome >= 0) store_mixed_cell<G>(L, l, cs, st, outcome);
   }
@@ -581,6 +717,7 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
 // Cell warps never wait for one another, and the network's 48 MMAs serve 16
 // cells.  Tags go after the data they cover (fence in between) and are read
 // before it.
+template <int NT>
 __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = L.S;
@@ -656,10 +793,7 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
 
   // ---- cell warps
   MixedCell cs = mixed_cell(L, cells + (size_t)warp * cell_bytes);
-  for (int i = l; i < S; i += 32) {
-    cs.Y[i] = 0.0;
-    cs.Yf[i] = 0.0f;
-  }
+  init_mixed_cell<32>(L, cs, l);
   const unsigned long long n = (unsigned long long)L.n_cells;
   CellState st = idle_cell_state();
   float Pf = (float)kPatm;
@@ -692,16 +826,16 @@ __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(La
     }
     idle_since = 0;
     idle_sleep = 1000u;
-    if (in_net_range(st.T)) {
+    if (in_net_range(st.Th)) {
       ++tag;  // warp-uniform
       if (l == 0) {
-        *(volatile float*)&sT[warp] = ((float)st.T - kTMid) / kTHalf;
+        *(volatile float*)&sT[warp] = (st.Th - kTMid) / kTHalf;
         __threadfence_block();
         *(volatile int*)&tag_req[warp] = tag;
       }
       __syncwarp();
     }
-    const int outcome = step_mixed<32, true>(L, tb, cs.Y, cs.Yf, cs.G2, cs.C, cs.H, cs.Q,
+    const int outcome = step_mixed<32, true, NT>(L, tb, cs.Yh, cs.Yl, cs.G2, cs.C, cs.H, cs.Q,
                                              cs.Hist, cs.Rof, Pf, l, st, cs.Th,
                                              tag_ans + warp, tag);
     if (outcome >= 0) store_mixed_cell<32>(L, l, cs, st, outcome);
