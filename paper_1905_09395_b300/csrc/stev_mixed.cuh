@@ -182,14 +182,16 @@ __device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, 
   const int S = L.S;
   const float Tf = T.h;
   if (use_net) {
-    bool answered = *net_ans == net_tag;
-    if (!__all_sync(0xffffffffu, answered) && l == 0)
-      net_ans[32] = net_tag;  // waiting: the evaluator answers at once (row + 32 = wait tags)
-    for (int k = 0; !answered && k < (1 << 18); ++k) {
-      __nanosleep(64);
-      answered = *net_ans == net_tag;
+    // the warp polls the answer tag together (bounded), so that the loop and
+    // its exit are warp-uniform
+    bool answered = __all_sync(0xffffffffu, *net_ans == net_tag);
+    if (!answered) {
+      if (l == 0) net_ans[32] = net_tag;  // waiting: the evaluator answers at once (row + 32 = wait tags)
+      for (int k = 0; !answered && k < (1 << 18); ++k) {
+        __nanosleep(64);
+        answered = __all_sync(0xffffffffu, *net_ans == net_tag);
+      }
     }
-    answered = __all_sync(0xffffffffu, answered);
     __threadfence_block();
     if (answered) {
       for (int i = l; i < S; i += G) {
@@ -305,6 +307,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
   // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e = sum nu g2, summed
   // exactly
   const int ktap = st.nhist % N;
+#pragma unroll(MLP ? 1 : 2)  // two reactions per trip where it pays (measured)
   for (int r = l; r < R; r += G) {
     const float4 rx = tb.rxf[r];
     const int4 ri = tb.ri[r];
