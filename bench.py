@@ -40,14 +40,18 @@ N_CELLS = 1 << 20
 # FP64-pipe cost of CUDA's exp() and log() in DFMA-equivalents, measured on
 # B300 by csrc/alu_peaks.cu (dfma 1.667/clk/SM, exp 0.104, log 0.055, div 0.222)
 EXP_OPS, LOG_OPS, DIV_OPS = 16.0, 30.0, 7.5
-# FP64 pipe peak: 1.667 DFMA/clk/SM x 148 SMs at the probe's 1919 MHz under load
-FP64_PEAK_OPS = 4.733e11
+# Arithmetic rates per SM and clock measured on B300 by csrc/alu_peaks.cu:
+# DFMA, FFMA, MUFU (ex2.approx) lane operations; the BF16 tensor rate from the
+# measured cuBLAS burst peak (1742.6 TFLOP/s at 2032 MHz).  Peaks are taken at
+# the SM clock sampled during the timed region.
+DFMA_PER_CLK, FFMA_PER_CLK, MUFU_PER_CLK = 1.668, 125.36, 31.66
+BF16_FLOP_PER_CLK = 1742.6e12 / (148 * 2032e6)
+N_SMS = 148
 # DRAM bytes per cell of one launch, from the ncu captures summarised in
-# profiles/ (3,108-, 2,960- and 1,628-cell cases of 300 steps; reads only: the
+# profiles/ (3,256-, 2,960- and 1,628-cell cases of 300 steps; reads only: the
 # small cases' output writes stay in L2), scaled to the full launch by the
-# cells it processes.  Set to None when the kernel changes after the capture.
-DRAM_BYTES_PER_CELL = {"mixed": 930048 / 3108, "fp64": 865536 / 1628,
-                       "mixed+mlp": 914688 / 2960}
+# cells it processes.  None when the kernel changed after its capture.
+DRAM_BYTES_PER_CELL = {"mixed": 966912 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 910080 / 2960}
 
 
 def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
@@ -70,13 +74,41 @@ def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
     return species + reactions + gather + dft + scalars
 
 
-def mixed_fp64_ops_per_cell_step(S: int) -> float:
-    """FP64 work the mixed-precision plan itself requires per cell-step, in
-    DFMA-equivalents: per species G/RT (7) and its split into a float pair (2)
-    and the FP64 Euler update with its conversion (2); per cell log T, 1/T and
-    the h / t_rem / T bookkeeping (~10).  Everything else runs on the FP32 and
-    MUFU pipes, which have 64x and 16x the FP64 pipe's rate."""
-    return S * (7 + 2 + 2) + LOG_OPS + DIV_OPS + 10
+def mixed_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int, net: bool = False) -> float:
+    """Algorithmic work of one mixed-precision STEV iteration of one cell, in
+    FP32-FMA-equivalents: the method's operations as counted by
+    fp64_ops_per_cell_step, placed on the mixed plan's units (the composite
+    bound t = flops / peak_fp + exps / peak_mufu + mma_flops / peak_bf16):
+    plain operations on the FP32 pipe; two exponentials per reaction, one
+    reciprocal per species (gamma), the scalar reciprocals and lg2 T on MUFU,
+    weighted by the measured FFMA / MUFU rate ratio; with the thermo network,
+    its per-cell MMA flops (1 x 64 x 64 and 64 x S for cp/R) weighted by the
+    BF16 tensor rate, in place of the cp polynomial."""
+    fma = (S * (4 + 6 + 7 + 3 + 3 + 1 + 3 + 4 + 1) + R * (2 + 2 + 3 + 2 + 2) + nnz +
+           Rrev * (1 + 12 + 3) + 12 + 3)
+    mufu = 2 * R + S + 3 + 1
+    ops = fma + mufu * FFMA_PER_CLK / MUFU_PER_CLK
+    if net:
+        ops -= 4 * S
+        ops += 2 * (64 * 64 + 64 * S) / BF16_FLOP_PER_CLK * FFMA_PER_CLK
+    return ops
+
+
+def alu_roofline(precision: str, ops: float, cell_steps: float, seconds: float,
+                 sm_mhz: float) -> dict:
+    """Composite ALU roofline: achieved = ops x cell-steps / s (FMA = 2 flops),
+    peak = the pipe's measured rate per SM and clock x SMs x the SM clock
+    sampled during the run."""
+    mhz = sm_mhz or 2032.0
+    per_clk = DFMA_PER_CLK if precision == "fp64" else FFMA_PER_CLK
+    peak = per_clk * N_SMS * mhz * 1e6
+    achieved = ops * cell_steps / seconds
+    return {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * peak / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / peak, "ops_per_cell_step": ops,
+            "pipe": ("fp64: DFMA %.3f/clk/SM" % DFMA_PER_CLK if precision == "fp64" else
+                     "fp32 composite: FFMA %.2f/clk/SM, MUFU %.2f/clk/SM as FFMA-equivalents"
+                     % (FFMA_PER_CLK, MUFU_PER_CLK)) +
+                    " (csrc/alu_peaks.cu) x %d SMs x %.0f MHz sampled" % (N_SMS, mhz)}
 
 
 def workload(n_cells: int, rank: int = 0):
@@ -605,7 +637,8 @@ def run_ours(args):
         mlp_info = {"net": "1-64-64-%d tanh, BF16 weights, FP32 accumulate" % (3 * S),
                     "train_samples": args.mlp_samples, "epochs": args.mlp_epochs,
                     "final_loss": float(hist[-1]), "train_s": time.time() - t0,
-                    "supplies": "cp/R and H/RT (energy equation), 300-3000 K"}
+                    "supplies": "cp/R (energy equation), 300-3000 K; H/RT and G/RT from the "
+                                "NASA-7 polynomials"}
     n = len(T)
     Td, Pd, Yd = (torch.from_numpy(a).to(dev) for a in (T, P, Y))
     out = (torch.empty_like(Td), torch.empty_like(Yd), torch.empty(n, dtype=torch.int32, device=dev),
@@ -646,54 +679,55 @@ def run_ours(args):
     trained_scale = m.mlp_params() if args.thermo == "mlp" else None
     m.close()
 
-    def one_solve(mc, ops):
+    clocks = clk.summary()
+
+    def one_solve(mc, precision, ops):
         """One timed solve of the same cells by another configuration."""
-        msx, _, _ = timed_solves(mc, Td, Pd, Yd, dt, out, 1, args.warmup, args.warmup_cells,
-                                 stream, dist)
+        with ClockSampler(local) as ck:
+            msx, _, _ = timed_solves(mc, Td, Pd, Yd, dt, out, 1, args.warmup, args.warmup_cells,
+                                     stream, dist)
         itx = out[2].cpu().numpy().astype(np.int64)
         tx = max_over_ranks(dist, msx[0] / 1e3, dev)
-        ach = ops * int(itx.sum()) / (msx[0] / 1e3)
+        ckx = ck.summary()
         return {"value": whole_job_rate(dist, msx[0] / 1e3, n, dev), "unit": UNIT,
                 "ms_per_step": tx * 1e3, "steps": 1,
                 "warmup": args.warmup, "cell_steps_per_s": int(itx.sum()) / tx,
-                "roofline": {"bound": "alu", "achieved": 2 * ach / 1e12,
-                             "peak": 2 * FP64_PEAK_OPS / 1e12, "unit": "TFLOP/s",
-                             "frac": ach / FP64_PEAK_OPS, "traffic": None,
-                             "ops_per_cell_step": ops}}
+                "roofline": dict(alu_roofline(precision, ops, int(itx.sum()), msx[0] / 1e3,
+                                              ckx["sm_mhz"]), traffic=None),
+                "clocks": ckx}
 
     # the same cells with the polynomial thermo (what the network gains) and
     # with the plain FP64 path (what mixed precision gains)
     mixed_poly, plain = None, None
     if args.precision == "mixed" and args.thermo == "mlp" and not args.no_poly_compare:
         mp = Mechanism(mech, precision=binding.MIXED, **extra)
-        mixed_poly = one_solve(mp, mixed_fp64_ops_per_cell_step(S))
+        mixed_poly = one_solve(mp, "mixed", mixed_ops_per_cell_step(S, R, Rrev, nnz))
         mp.close()
     if args.precision == "mixed" and not args.no_fp64_compare:
         mf = Mechanism(mech, precision=binding.FP64, **extra)
-        plain = one_solve(mf, fp64_ops_per_cell_step(S, R, Rrev, nnz))
+        plain = one_solve(mf, "fp64", fp64_ops_per_cell_step(S, R, Rrev, nnz))
         plain_head = [x[:4096].cpu().numpy() for x in out]
         mf.close()
 
     if rank != 0:
         return 0
     if args.precision == "mixed":
-        ops = mixed_fp64_ops_per_cell_step(S)
-        ops_note = ("FP64 work the mixed plan requires (species G/RT and split, FP64 Euler, "
-                    "log T, 1/T, step bookkeeping); FP32/MUFU work not counted")
+        ops = mixed_ops_per_cell_step(S, R, Rrev, nnz, net=args.thermo == "mlp")
+        ops_note = ("the method's operations on the mixed plan's units (FP32 pipe; exps, "
+                    "reciprocals and lg2 T on MUFU%s), in FFMA-equivalents"
+                    % ("; the network's MMA flops on the BF16 tensor rate"
+                       if args.thermo == "mlp" else ""))
     else:
         ops = fp64_ops_per_cell_step(S, R, Rrev, nnz)
         ops_note = ("the method's FP64 work: exp = %g, log = %g, div = %g DFMA-equivalents, "
                     "measured" % (EXP_OPS, LOG_OPS, DIV_OPS))
-    achieved = ops * cell_steps / (float(np.mean(ms)) / 1e3)
     bpc = DRAM_BYTES_PER_CELL.get(args.precision + ("+mlp" if args.thermo == "mlp" else ""))
-    roofline = {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * FP64_PEAK_OPS / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_OPS,
-                "traffic": None if bpc is None else bpc * n,
-                "traffic_note": "DRAM bytes per launch scaled from the ncu capture in profiles/",
-                "pipe": "fp64 (DFMA = 2 flops); peak = measured DFMA rate of csrc/alu_peaks.cu "
-                        "(1.667/clk/SM x 148 SMs x 1919 MHz)",
-                "ops_per_cell_step": ops, "ops_counted": ops_note,
-                "cell_steps_per_launch": cell_steps}
+    roofline = alu_roofline(args.precision, ops, cell_steps, float(np.mean(ms)) / 1e3,
+                            clocks["sm_mhz"])
+    roofline.update({"traffic": None if bpc is None else bpc * n,
+                     "traffic_note": "DRAM bytes per launch scaled from the ncu capture in "
+                                     "profiles/ by the cells processed",
+                     "ops_counted": ops_note, "cell_steps_per_launch": cell_steps})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -717,7 +751,7 @@ def run_ours(args):
             "roofline": roofline, "gpu_launches": args.steps, "e2e": e2e,
             "mixed_poly": mixed_poly, "plain_fp64": plain, "thermo_net": mlp_info,
             "wall_s_timed": wall}
-    line["clocks"] = clk.summary()
+    line["clocks"] = clocks
     if world == 1 and not args.no_serve and args.precision == "mixed" and args.thermo == "mlp":
         # p50/p99 latency under the serving load (the scale mechanism's network reused)
         sv = serve_arm("mixed+mlp", args, trained=[None, trained_scale])
