@@ -33,7 +33,7 @@ constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
 constexpr int kNone = 0xFF;
 constexpr int kMaxBlock = 512;       // threads per CTA of the FP64 persistent kernel
 constexpr int kMaxBlockMixed = 768;  // threads per CTA of the mixed persistent kernel
-constexpr int kMaxBlockMixedNet = 704;  // ... with the thermo network: 20 cell warps + 2 evaluators
+constexpr int kMaxBlockMixedNet = 768;  // ... with the thermo network: cell warps + 2 evaluators
 
 enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
