@@ -94,6 +94,12 @@ def mixed_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int, net: bool = Fal
     return ops
 
 
+def spec_flag(args) -> int:
+    """Mixed-precision mechanisms run the kernel compiled for them (NVRTC at
+    creation, outside the timed region) unless --generic."""
+    return 0 if getattr(args, "generic", False) else 1
+
+
 def alu_roofline(precision: str, ops: float, cell_steps: float, seconds: float,
                  sm_mhz: float) -> dict:
     """Composite ALU roofline: achieved = ops x cell-steps / s (FMA = 2 flops),
@@ -317,7 +323,7 @@ def run_uneven(args):
     dev = torch.device("cuda", 0)
     mech, host_batches, dt = synth.uneven_case(args.uneven_scale)
     extra = {} if args.max_iters is None else {"max_iters": args.max_iters}
-    m = Mechanism(mech, precision=binding.MIXED, **extra)
+    m = Mechanism(mech, precision=binding.MIXED, specialize=spec_flag(args), **extra)
     info = None
     if args.thermo == "mlp":
         t0 = time.time()
@@ -377,7 +383,8 @@ def _serve_mechanisms(arm, args, trained=None):
     from paper_1905_09395_b300 import Mechanism, binding, synth
     tabs = [synth.small_mechanism(), synth.scale_mechanism()]
     prec = binding.MIXED if arm == "mixed+mlp" else binding.FP64
-    ms = [Mechanism(t, precision=prec) for t in tabs]
+    ms = [Mechanism(t, precision=prec, specialize=spec_flag(args) if arm == "mixed+mlp" else 0)
+          for t in tabs]
     if arm == "mixed+mlp":
         Ts = np.random.default_rng(2024).uniform(300.0, 3000.0, size=args.mlp_samples)
         for i, m in enumerate(ms):
@@ -558,8 +565,8 @@ def run_bfer(args):
     stream = torch.cuda.current_stream(dev)
     arms = {}
     with ClockSampler(0) as clk:
-        for name, kw in (("mixed+mlp", dict(precision=binding.MIXED)),
-                         ("mixed_poly", dict(precision=binding.MIXED)),
+        for name, kw in (("mixed+mlp", dict(precision=binding.MIXED, specialize=spec_flag(args))),
+                         ("mixed_poly", dict(precision=binding.MIXED, specialize=spec_flag(args))),
                          ("plain_fp64", dict(precision=binding.FP64))):
             m = Mechanism(mech, **kw)
             info = None
@@ -625,7 +632,8 @@ def run_ours(args):
     Rrev, nnz = int(mech.reversible.sum()), len(mech.rxn_species)
     extra = {} if args.max_iters is None else {"max_iters": args.max_iters}
     prec = binding.MIXED if args.precision == "mixed" else binding.FP64
-    m = Mechanism(mech, precision=prec, **extra)
+    m = Mechanism(mech, precision=prec, specialize=spec_flag(args) if prec == binding.MIXED else 0,
+                  **extra)
     mlp_info = None
     if args.precision != "mixed":
         args.thermo = "poly"
@@ -700,7 +708,7 @@ def run_ours(args):
     # with the plain FP64 path (what mixed precision gains)
     mixed_poly, plain = None, None
     if args.precision == "mixed" and args.thermo == "mlp" and not args.no_poly_compare:
-        mp = Mechanism(mech, precision=binding.MIXED, **extra)
+        mp = Mechanism(mech, precision=binding.MIXED, specialize=spec_flag(args), **extra)
         mixed_poly = one_solve(mp, "mixed", mixed_ops_per_cell_step(S, R, Rrev, nnz))
         mp.close()
     if args.precision == "mixed" and not args.no_fp64_compare:
@@ -738,6 +746,8 @@ def run_ours(args):
                                    "dt 1e-3 s" % n,
                        "precision": args.precision,
                        "thermo": "network" if args.thermo == "mlp" else "NASA-7 polynomial",
+                       "kernel": ("compiled for the mechanism (NVRTC)" if args.precision == "mixed"
+                                  and spec_flag(args) else "generic"),
                        "cells_per_gpu": n, "warmup_cells": nw, "max_iters": extra.get(
                            "max_iters", 200000),
                        "l2": "inputs (%d MB) larger than L2" % ((T.nbytes + P.nbytes + Y.nbytes)
@@ -812,6 +822,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--generic", action="store_true",
+                    help="mixed precision: the generic kernel instead of the one compiled for "
+                         "the mechanism")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -53,7 +53,8 @@ enum { STEV_FP64 = 0, STEV_MIXED = 1 };            /* options.precision */
 /* options.thermo: where the mixed path takes species properties from.
  * POLY: NASA-7 polynomials.  MLP: cp/R from the thermo network, H/RT and G/RT
  * from the polynomials.  MLP_CPH: cp/R and H/RT from the network.  G/RT (the
- * equilibrium constants of Eq. 30) always comes from the FP64 polynomials. */
+ * equilibrium constants of Eq. 30) always comes from the polynomials, at
+ * FP64-grade precision. */
 enum { STEV_THERMO_POLY = 0, STEV_THERMO_MLP = 1, STEV_THERMO_MLP_CPH = 2 };
 
 /* Solver parameters.  The paper names them but gives values for few; the
@@ -74,6 +75,12 @@ typedef struct {
   int dft_on;         /* 0 disables the Sec. 2.3 damper (1) */
   int lanes_per_cell; /* lanes that share one cell: 8, 16 or 32; 0 = chosen per
                          mechanism and precision (0) */
+  int specialize;     /* mixed precision: 1 compiles the solver kernel for this
+                         mechanism at run time (NVRTC; its sizes and rate-law
+                         kind as constants, SURVEY's per-mechanism kernels),
+                         a few seconds at creation or when the options change;
+                         0 uses the generic kernel (0).  Needs the csrc
+                         directory beside the library and CUDA's headers. */
 } stev_options;
 
 /* Fills *opt with the defaults above.  Never fails for a non-NULL opt. */
@@ -361,6 +368,21 @@ long long stev_mlp_stalls(const stev_mechanism *mech);
 /* Number of resident solver slots (cells in flight) of the persistent kernel
  * on the current device for this mechanism and its options. */
 long stev_resident_slots(const stev_mechanism *mech);
+
+/* 1 if this mechanism's solves run a kernel specialised for it
+ * (options.specialize with mixed precision), 0 if the generic kernel. */
+int stev_is_specialized(const stev_mechanism *mech);
+
+/* Compiles (NVRTC, for sm_103a) the mixed-precision kernel specialised for
+ * these sizes without loading it: no GPU is needed.  general: real orders or
+ * stoichiometry; lanes_per_cell: 8, 16 or 32 (32 with network = 1); dft_n:
+ * 13 selects the unrolled window, any other value the run-time one.  NVRTC's
+ * log is copied into log[log_len] (may be NULL).  STEV_EINVAL for sizes out
+ * of range, STEV_ECUDA if the compilation fails (its log in
+ * stev_last_error()). */
+stev_status stev_spec_compile_check(int n_species, int n_reactions, int n_reversible,
+                                    int general, int lanes_per_cell, int dft_n, int network,
+                                    char *log, size_t log_len);
 
 /* Frees a mechanism and everything it owns.  NULL is a no-op.  Waits for
  * outstanding work of the mechanism to finish. */

@@ -32,6 +32,7 @@ EXPORTS = (
     "stev_server_create", "stev_server_submit", "stev_server_poll", "stev_server_get_stats",
     "stev_server_clock", "stev_server_stop", "stev_server_destroy", "stev_mlp_stalls",
     "stev_mlp_train_lm", "stev_mlp_jacobian", "stev_mechanism_create_orders",
+    "stev_is_specialized", "stev_spec_compile_check",
 )
 
 
@@ -48,7 +49,7 @@ class Options(ctypes.Structure):
         ("tol_ring", ctypes.c_double), ("tol_freq", ctypes.c_double),
         ("r_fac", ctypes.c_double), ("rof_min", ctypes.c_double), ("max_iters", ctypes.c_int),
         ("precision", ctypes.c_int), ("thermo", ctypes.c_int), ("dft_on", ctypes.c_int),
-        ("lanes_per_cell", ctypes.c_int),
+        ("lanes_per_cell", ctypes.c_int), ("specialize", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -135,6 +136,10 @@ def lib():
         L.stev_mlp_stalls.restype = ctypes.c_longlong
         L.stev_resident_slots.argtypes = [P]
         L.stev_resident_slots.restype = LNG
+        L.stev_is_specialized.argtypes = [P]
+        L.stev_is_specialized.restype = I
+        L.stev_spec_compile_check.argtypes = [I, I, I, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t]
+        L.stev_spec_compile_check.restype = I
         L.stev_destroy.argtypes = [P]
         L.stev_destroy.restype = None
         L.stev_last_error.argtypes = []
@@ -223,6 +228,11 @@ class Mechanism:
     @property
     def resident_slots(self) -> int:
         return int(lib().stev_resident_slots(self._h))
+
+    @property
+    def is_specialized(self) -> bool:
+        """True when the solves run a kernel compiled for this mechanism."""
+        return bool(lib().stev_is_specialized(self._h))
 
     # -- device entry points ----------------------------------------------------
     def _check_dev(self, T, P, Y, soa):
@@ -464,3 +474,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def spec_compile_check(n_species: int, n_reactions: int, n_reversible: int, general: bool = False,
+                       lanes_per_cell: int = 32, dft_n: int = 13, network: bool = False) -> str:
+    """Compiles the per-mechanism kernel for these sizes (no GPU needed) and
+    returns NVRTC's log; raises StevError if it does not compile."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().stev_spec_compile_check(int(n_species), int(n_reactions), int(n_reversible),
+                                         int(bool(general)), int(lanes_per_cell), int(dft_n),
+                                         int(bool(network)), buf, len(buf)))
+    return buf.value.decode(errors="replace")

@@ -97,6 +97,12 @@ struct stev_mechanism {
   __nv_bfloat16* d_mlp_W3 = nullptr;      // [out_pad][64]
   float* d_mlp_misc = nullptr;            // W1, b1, b2 [64 each], b3, mean, std [out_pad each]
   bool mlp_ready = false;
+  // the solver kernel: the generic instantiation, or one compiled for this
+  // mechanism (options.specialize)
+  const void* kfn = nullptr;
+  cudaLibrary_t spec_lib = nullptr;
+  cudaKernel_t spec_k = nullptr;
+  stev::host::SpecKey spec_key{};
 };
 
 extern "C" void stev_default_options(stev_options* o) {
@@ -115,6 +121,7 @@ extern "C" void stev_default_options(stev_options* o) {
   o->thermo = STEV_THERMO_POLY;
   o->dft_on = 1;
   o->lanes_per_cell = 0;
+  o->specialize = 0;
 }
 
 static stev_status check_options(const stev_options* o) {
@@ -137,6 +144,7 @@ static stev_status check_options(const stev_options* o) {
     return fail(STEV_EINVAL, "lanes_per_cell must be 0, 8, 16 or 32");
   if (o->thermo != STEV_THERMO_POLY && o->precision != STEV_MIXED)
     return fail(STEV_EINVAL, "the thermo network is used by the mixed-precision path only");
+  if (o->specialize != 0 && o->specialize != 1) return fail(STEV_EINVAL, "specialize must be 0 or 1");
   return STEV_OK;
 }
 
@@ -147,6 +155,7 @@ static void free_mech(stev_mechanism* m) {
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (m->spec_lib) cudaLibraryUnload(m->spec_lib);
   delete m;
 }
 
@@ -211,10 +220,25 @@ static stev_status configure(stev_mechanism* m) {
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
   const size_t smem = tables + (size_t)cells * cell + (net ? net_cta_smem_bytes(cells) : 0);
   const int block = cells * G + (net ? 32 * net_evaluators(cells) : 0);
-  KernelFn k = select_kernel(m->opt.precision, G, m->opt.thermo, m->opt.dft_n);
+  const void* k = reinterpret_cast<const void*>(select_kernel(m->opt.precision, G, m->opt.thermo,
+                                                              m->opt.dft_n));
+  if (mixed && m->opt.specialize) {
+    const stev::host::SpecKey key{m->S, m->R, m->Rrev, m->general, G,
+                                  m->opt.dft_n == 13 ? 13 : 0, net ? 1 : 0};
+    if (!m->spec_k || !(key == m->spec_key)) {
+      if (m->spec_lib) cudaLibraryUnload(m->spec_lib);
+      m->spec_lib = nullptr;
+      m->spec_k = nullptr;
+      const stev_status st = stev::host::spec_load(key, &m->spec_lib, &m->spec_k);
+      if (st != STEV_OK) return st;
+      m->spec_key = key;
+    }
+    k = reinterpret_cast<const void*>(m->spec_k);
+  }
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
+  m->kfn = k;
   if (per_sm < 1) return fail(STEV_EINVAL, "persistent kernel cannot be resident");
   m->block = block;
   m->cells = cells;
@@ -518,6 +542,10 @@ extern "C" stev_status stev_mechanism_get_options(const stev_mechanism* m, stev_
 
 extern "C" long stev_resident_slots(const stev_mechanism* m) { return m ? (long)m->nslots : 0; }
 
+extern "C" int stev_is_specialized(const stev_mechanism* m) {
+  return m && m->spec_k && m->kfn == reinterpret_cast<const void*>(m->spec_k) ? 1 : 0;
+}
+
 extern "C" long long stev_mlp_stalls(const stev_mechanism* m) {
   if (!m || !m->d_net_stalls) return 0;
   unsigned long long v = 0;
@@ -595,10 +623,20 @@ static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, co
   return STEV_OK;
 }
 
+// Launches the mechanism's solver kernel (generic or specialised) with the
+// launch configuration chosen by configure().
+static cudaError_t launch_solver(const stev_mechanism* m, int grid, const Launch& L,
+                                 cudaStream_t s) {
+  Launch arg = L;
+  void* args[] = {&arg};
+  const cudaError_t e =
+      cudaLaunchKernel(m->kfn, dim3((unsigned)grid), dim3((unsigned)m->block), args, m->smem, s);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 static stev_status launch_persistent(stev_mechanism* m, const Launch& L, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned long long), s));
-  select_kernel(m->opt.precision, m->G, m->opt.thermo, m->opt.dft_n)<<<m->grid, m->block, m->smem, s>>>(L);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_solver(m, m->grid, L, s));
   return STEV_OK;
 }
 
@@ -746,8 +784,7 @@ stev_status serve_launch(stev_mechanism* m, ServeCtl* ctl, ServeSlot* slots,
   L.serve_warps = grid * (m->cells * m->G / 32);  // warps holding cells
   L.y_soa = 0;
   CUDA_TRY(cudaMemsetAsync(&ctl->idle_warps, 0, 2 * sizeof(int), s));  // idle_warps, exiting
-  select_kernel(m->opt.precision, m->G, m->opt.thermo, m->opt.dft_n)<<<grid, m->block, m->smem, s>>>(L);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_solver(m, grid, L, s));
   return STEV_OK;
 }
 
@@ -851,8 +888,7 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
   L.T_out = dTo; L.Y_out = dYo; L.iters = dit; L.status = dst;
   L.y_soa = 0;
   L.counter = counter;
-  select_kernel(m->opt.precision, m->G, m->opt.thermo, m->opt.dft_n)<<<m->grid, m->block, m->smem, s>>>(L);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_solver(m, m->grid, L, s));
   CUDA_TRY(cudaMemcpyAsync(T_out, dTo, nn * 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(Y_out, dYo, nn * m->S * 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(iters, dit, nn * 4, cudaMemcpyDeviceToHost, s));

@@ -18,7 +18,9 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#ifndef __CUDACC_RTC__  // run-time compiled copies (stev_spec.cu) get these from NVRTC
 #include <cstdint>
+#endif
 
 #include "stev_layout.h"
 

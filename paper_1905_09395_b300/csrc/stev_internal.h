@@ -4,6 +4,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
+#include <vector>
+
 #include "../../include/stev.h"
 #include "stev_layout.h"
 
@@ -33,6 +36,24 @@ stev_status serve_config(const stev_mechanism* m, ServeConfig* out);
 stev_status serve_launch(stev_mechanism* m, ServeCtl* ctl, ServeSlot* slots,
                          volatile long long* mail, int q, long long idle_ns, int grid,
                          cudaStream_t s);
+
+// A mixed-precision kernel specialised for one mechanism (stev_spec.cu):
+// sizes, rate-law kind, lanes per cell, DFT window (13 or 0 = run time) and
+// whether it is the thermo-network kernel.
+struct SpecKey {
+  int S, R, Rrev, general, G, NT, net;
+  bool operator==(const SpecKey& o) const {
+    return S == o.S && R == o.R && Rrev == o.Rrev && general == o.general && G == o.G &&
+           NT == o.NT && net == o.net;
+  }
+};
+
+// Compiles the specialised kernel with NVRTC for sm_103a; the CUBIN and its
+// lowered name on success, NVRTC's log in any case.  Needs no GPU.
+stev_status spec_compile(const SpecKey& k, std::vector<char>* cubin, std::string* lowered,
+                         std::string* log);
+// Compiles and loads it into the current device's primary context.
+stev_status spec_load(const SpecKey& k, cudaLibrary_t* lib, cudaKernel_t* kernel);
 
 }  // namespace host
 }  // namespace stev

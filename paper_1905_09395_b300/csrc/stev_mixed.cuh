@@ -33,6 +33,21 @@ namespace stev {
 
 constexpr double kLog2e = 1.4426950408889634;
 
+// Mechanism sizes and the rate-law kind: compile-time constants in a kernel
+// built for one mechanism (STEV_SPEC_S, _R, _RREV, _GENERAL defined: loops of
+// known trip count, table rows at immediate offsets), else the launch's.
+#ifdef STEV_SPEC_S
+__device__ __forceinline__ constexpr int mS(const Launch&) { return STEV_SPEC_S; }
+__device__ __forceinline__ constexpr int mR(const Launch&) { return STEV_SPEC_R; }
+__device__ __forceinline__ constexpr int mRrev(const Launch&) { return STEV_SPEC_RREV; }
+__device__ __forceinline__ constexpr int mGeneral(const Launch&) { return STEV_SPEC_GENERAL; }
+#else
+__device__ __forceinline__ int mS(const Launch& L) { return L.S; }
+__device__ __forceinline__ int mR(const Launch& L) { return L.R; }
+__device__ __forceinline__ int mRrev(const Launch& L) { return L.Rrev; }
+__device__ __forceinline__ int mGeneral(const Launch& L) { return L.general; }
+#endif
+
 __device__ __forceinline__ float ex2f(float x) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -179,7 +194,7 @@ __device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, 
                                             float* cH, const float* cTh,
                                             volatile int* net_ans, int net_tag,
                                             bool use_net, FF T, float invTf, int l, float cpp) {
-  const int S = L.S;
+  const int S = mS(L);
   const float Tf = T.h;
   if (use_net) {
     // the warp polls the answer tag together (bounded), so that the loop and
@@ -240,7 +255,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
                                           CellState& st, const float* cTh,
                                           volatile int* net_ans, int net_tag) {
-  const int S = L.S, R = L.R, Rrev = L.Rrev;
+  const int S = mS(L), R = mR(L), Rrev = mRrev(L);
   const int N = NT > 0 ? NT : L.dft_n;
   const int NP = N | 1;
   const FF T{st.Th, st.Tl};
@@ -314,7 +329,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     const int a0 = ri.x & 0xFF, a1 = (ri.x >> 8) & 0xFF;
     const int p0 = (ri.x >> 16) & 0xFF, p1 = (ri.x >> 24) & 0xFF;
     const float lg2kf = fmaf(rx.y, lg2Tf, rx.x) - rx.z * invTf;
-    if (L.general) {
+    if (mGeneral(L)) {
       // real stoichiometry and orders: C^a = 2^(a lg2 C); the exponent
       // x = sum nu g2 of Eq. 30 summed exactly with the products' errors
       // (an unused slot: species S, lg2 C = 0, order and nu 0)
@@ -368,12 +383,12 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
 
   // production rates, dY/dt, dT/dt terms and the limiter (FP32)
   const float invRho = 1.0f / rho;
-  float hwp = 0.0f, tmin = INFINITY;
+  float hwp = 0.0f, tmin = __int_as_float(0x7f800000);  // +inf
   for (int i = l; i < S; i += G) {
     float wd = 0.0f;
     for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
       const int e = tb.gent[k];
-      wd = fmaf(L.general ? tb.gnu[k] : kNuOfF[e & 15], cQ[e >> 4], wd);
+      wd = fmaf(mGeneral(L) ? tb.gnu[k] : kNuOfF[e & 15], cQ[e >> 4], wd);
     }
     const float ri = tb.spf[SF_W * S + i] * wd * invRho;
     hwp = fmaf(cH[i], wd, hwp);
@@ -512,34 +527,34 @@ struct MixedCell {
 __device__ __forceinline__ MixedCell mixed_cell(const Launch& L, unsigned char* base) {
   MixedCell c;
   c.G2 = reinterpret_cast<float2*>(base);  // S + 1 (the unused-slot entry)
-  c.Yh = reinterpret_cast<float*>(c.G2 + L.S + 1);
-  c.Yl = c.Yh + L.S;
-  c.C = c.Yl + L.S;                        // S + 1
-  c.H = c.C + L.S + 1;
-  c.Q = c.H + L.S;
-  c.Hist = c.Q + L.R;                      // [Rrev][N | 1]
-  c.Rof = c.Hist + (L.dft_n | 1) * L.Rrev;
-  c.Th = c.Rof + L.Rrev;
+  c.Yh = reinterpret_cast<float*>(c.G2 + mS(L) + 1);
+  c.Yl = c.Yh + mS(L);
+  c.C = c.Yl + mS(L);                        // S + 1
+  c.H = c.C + mS(L) + 1;
+  c.Q = c.H + mS(L);
+  c.Hist = c.Q + mR(L);                      // [Rrev][N | 1]
+  c.Rof = c.Hist + (L.dft_n | 1) * mRrev(L);
+  c.Th = c.Rof + mRrev(L);
   return c;
 }
 
 // Zeroes a cell block's Y and sets the unused-slot entries (C = 1, g2 = 0).
 template <int G>
 __device__ __forceinline__ void init_mixed_cell(const Launch& L, const MixedCell& cs, int l) {
-  for (int i = l; i < L.S; i += G) {
+  for (int i = l; i < mS(L); i += G) {
     cs.Yh[i] = 0.0f;
     cs.Yl[i] = 0.0f;
   }
   if (l == 0) {
-    cs.C[L.S] = 1.0f;
-    cs.G2[L.S] = make_float2(0.0f, 0.0f);
+    cs.C[mS(L)] = 1.0f;
+    cs.G2[mS(L)] = make_float2(0.0f, 0.0f);
   }
   __syncwarp();
 }
 
 // Stages the mechanism tables of the mixed kernels in shared memory.
 __device__ __forceinline__ TablesF stage_tables_mixed(const Launch& L, unsigned char* smem_raw) {
-  const int S = L.S, R = L.R;
+  const int S = mS(L), R = mR(L);
   float4* s_rxf = reinterpret_cast<float4*>(smem_raw);
   int4* s_ri = reinterpret_cast<int4*>(s_rxf + R);
   float* s_spf = reinterpret_cast<float*>(s_ri + R);
@@ -554,7 +569,7 @@ __device__ __forceinline__ TablesF stage_tables_mixed(const Launch& L, unsigned 
   for (int t = threadIdx.x; t < L.n_gather; t += blockDim.x) s_gent[t] = L.g_ent[t];
   float* s_rg = nullptr;
   float* s_gnu = nullptr;
-  if (L.general) {  // after the 16-byte-aligned base tables
+  if (mGeneral(L)) {  // after the 16-byte-aligned base tables
     s_rg = reinterpret_cast<float*>(smem_raw + table_smem_bytes_mixed(S, R, L.n_gather,
                                                                       L.n_hi_bins, L.dft_n, 0));
     s_gnu = s_rg + R * 8;
@@ -607,7 +622,7 @@ __device__ __forceinline__ void load_mixed_cell(const Launch& L, long long c, in
     st.b = find_batch(L, c);
     st.lc = L.nb > 0 ? c - L.boff[st.b] : c;
   }
-  const int S = L.S;
+  const int S = mS(L);
   const CellIO io = cell_io(L, st.b);
   const long long lc = st.lc;
   st.cell = c;
@@ -626,14 +641,14 @@ __device__ __forceinline__ void load_mixed_cell(const Launch& L, long long c, in
     cs.Yh[i] = yf.h;
     cs.Yl[i] = yf.l;
   }
-  for (int w = l; w < L.Rrev; w += G) cs.Rof[w] = 1.0f;
+  for (int w = l; w < mRrev(L); w += G) cs.Rof[w] = 1.0f;
 }
 
 // Writes a finished cell's outputs and frees the group.
 template <int G>
 __device__ __forceinline__ void store_mixed_cell(const Launch& L, int l, MixedCell& cs,
                                                  CellState& st, int outcome) {
-  const int S = L.S;
+  const int S = mS(L);
   const CellIO io = cell_io(L, st.b);
   const long long c = st.lc;
   if (l == 0) {
@@ -654,13 +669,13 @@ __device__ __forceinline__ void store_mixed_cell(const Launch& L, int l, MixedCe
 template <int G, int NT>
 __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int S = L.S;
+  const int S = mS(L);
   const TablesF tb = stage_tables_mixed(L, smem_raw);
 
   const int group = threadIdx.x / G;
   const int l = threadIdx.x % G;
-  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n, L.general);
-  const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, false);
+  const size_t tables = table_smem_bytes_mixed(S, mR(L), L.n_gather, L.n_hi_bins, L.dft_n, mGeneral(L));
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, mR(L), mRrev(L), L.dft_n, false);
   MixedCell cs = mixed_cell(L, smem_raw + tables + (size_t)group * cell_bytes);
   init_mixed_cell<G>(L, cs, l);
 
@@ -723,14 +738,14 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
 template <int NT>
 __global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int S = L.S;
+  const int S = mS(L);
   const TablesF tb = stage_tables_mixed(L, smem_raw);
   const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int ncells = L.net_cells;  // <= 32
   const int nev = net_evaluators(ncells);
   const int per_ev = (ncells + nev - 1) / nev;  // rows each evaluator answers, <= 16
-  const size_t tables = table_smem_bytes_mixed(S, L.R, L.n_gather, L.n_hi_bins, L.dft_n, L.general);
-  const size_t cell_bytes = cell_smem_bytes_mixed(S, L.R, L.Rrev, L.dft_n, true);
+  const size_t tables = table_smem_bytes_mixed(S, mR(L), L.n_gather, L.n_hi_bins, L.dft_n, mGeneral(L));
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, mR(L), mRrev(L), L.dft_n, true);
   unsigned char* cells = smem_raw + tables;
   float* sT = reinterpret_cast<float*>(cells + (size_t)ncells * cell_bytes);
   int* tag_req = reinterpret_cast<int*>(sT + 32);

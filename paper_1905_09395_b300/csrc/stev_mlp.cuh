@@ -465,8 +465,10 @@ __global__ void mlp_eval_kernel(MlpInfer w, const double* __restrict__ T, long l
   }
 }
 
+#ifndef __CUDACC_RTC__
 __host__ inline size_t mlp_eval_smem_bytes(int warps) {
   return (size_t)warps * 16 * (kHid + 8) * 2 + (size_t)warps * 16 * 4;
 }
+#endif
 
 }  // namespace stev

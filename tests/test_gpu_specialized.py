@@ -1,0 +1,89 @@
+"""Per-mechanism specialised kernels (options.specialize = 1): the same
+mixed-precision solver compiled at run time with the mechanism's sizes as
+constants.  Step prefixes match the generic kernel's to FP32 rounding, full
+solves meet the mixed-precision target against the FP64 oracle like the
+generic kernel, and the network and global-rate-law variants run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_09395_b300 import FP64, MIXED, THERMO_MLP, Mechanism, synth
+from test_gpu_mixed import _check, _small_conditioning
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(m, T, P, Y, dt):
+    import torch
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (T, P, Y)]
+    return tuple(x.cpu().numpy() for x in m.solve(*d, dt))
+
+
+def _pair(mech, **opts):
+    gen = Mechanism(mech, precision=MIXED, **opts)
+    spec = Mechanism(mech, precision=MIXED, specialize=1, **opts)
+    assert spec.is_specialized and not gen.is_specialized
+    return gen, spec
+
+
+@pytest.mark.parametrize("which", ["small", "scale", "bfer"])
+def test_prefix_matches_generic(which):
+    if which == "small":
+        mech, T, P, Y, dt = synth.small_case(512)
+    elif which == "scale":
+        mech = synth.scale_mechanism()
+        T, P, Y = synth.make_cells(mech, 256, seed=11, T_range=(800, 2200), P_atm_range=(1, 5),
+                                   dirichlet=0.5)
+        dt = 1e-3
+    else:
+        mech = synth.bfer_mechanism()
+        T, P, Y = synth.bfer_cells(mech, 512)
+        dt = 1e-3
+    for k in (1, 14, 60):
+        gen, spec = _pair(mech, max_iters=k)
+        a, b = _run(gen, T, P, Y, dt), _run(spec, T, P, Y, dt)
+        gen.close()
+        spec.close()
+        assert (a[2] == b[2]).all() and (a[3] == b[3]).all()
+        assert np.abs(a[1] - b[1]).max() <= 1e-7, "k=%d" % k
+        assert np.abs(a[0] - b[0]).max() <= 1e-3, "k=%d" % k
+
+
+def test_full_solve_meets_the_mixed_target():
+    mech, T, P, Y, dt = synth.small_case(2048)
+    ref, sY, sT = _small_conditioning()
+    m = Mechanism(mech, precision=MIXED, specialize=1)
+    within = _check(mech, T, Y, _run(m, T, P, Y, dt), ref, sY, sT, "specialised mixed 8/20 x 2048")
+    assert within > 0.95
+    m.close()
+
+
+def test_network_kernel_specialised():
+    mech = synth.scale_mechanism()
+    T, P, Y = synth.make_cells(mech, 256, seed=11, T_range=(800, 2200), P_atm_range=(1, 5),
+                               dirichlet=0.5)
+    Ts = np.linspace(300.0, 3000.0, 200_000)
+    out = []
+    for spec in (0, 1):
+        m = Mechanism(mech, precision=MIXED, specialize=spec, max_iters=60)
+        m.mlp_train(Ts, epochs=4, batch=4096, lr=2e-3, seed=1)
+        m.set_options(thermo=THERMO_MLP)
+        assert m.is_specialized == bool(spec)
+        out.append(_run(m, T, P, Y, 1e-3))
+        assert m.mlp_stalls == 0
+        m.close()
+    a, b = out
+    assert (a[2] == b[2]).all() and (a[3] == b[3]).all()
+    assert np.abs(a[1] - b[1]).max() <= 1e-7
+
+
+def test_fp64_ignores_specialize():
+    mech, T, P, Y, dt = synth.small_case(64)
+    m = Mechanism(mech, precision=FP64, specialize=1)
+    assert not m.is_specialized
+    ref = oracle.solve(mech, T, P, Y, dt, max_iters=14)
+    m.set_options(max_iters=14)
+    To, Yo, it, st = _run(m, T, P, Y, dt)
+    assert (it == ref[2]).all()
+    assert np.abs(Yo - ref[1]).max() <= 1e-10
+    m.close()
