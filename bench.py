@@ -48,10 +48,10 @@ DFMA_PER_CLK, FFMA_PER_CLK, MUFU_PER_CLK = 1.668, 125.36, 31.66
 BF16_FLOP_PER_CLK = 1742.6e12 / (148 * 2032e6)
 N_SMS = 148
 # DRAM bytes per cell of one launch, from the ncu captures summarised in
-# profiles/ (3,256-, 2,960- and 1,628-cell cases of 300 steps; reads only: the
+# profiles/ (3,256-, 3,108- and 1,628-cell cases of 300 steps; reads only: the
 # small cases' output writes stay in L2), scaled to the full launch by the
 # cells it processes.  None when the kernel changed after its capture.
-DRAM_BYTES_PER_CELL = {"mixed": 966912 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 910080 / 2960}
+DRAM_BYTES_PER_CELL = {"mixed": 956416 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 939520 / 3108}
 
 
 def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
