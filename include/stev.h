@@ -49,7 +49,13 @@ enum {
   STEV_CELL_TRANGE = 3      /* T left [200, 6000] K; state at that step */
 };
 
-enum { STEV_FP64 = 0, STEV_MIXED = 1 };            /* options.precision */
+/* options.precision.  FP64: every quantity in IEEE double (the oracle's
+ * arithmetic).  MIXED: rates, limiter and ringing test in FP32 (base-2 MUFU
+ * exponentials); Y, T, ln T, 1/T and the species' Gibbs terms of Eq. 30 as
+ * float pairs (about 48 significant bits) on the FP32 pipe; h and t_rem in
+ * double.  Results of MIXED meet 1e-4 in Y and 0.5 K against FP64 on cells
+ * that are well-conditioned at single-precision rounding. */
+enum { STEV_FP64 = 0, STEV_MIXED = 1 };
 /* options.thermo: where the mixed path takes species properties from.
  * POLY: NASA-7 polynomials.  MLP: cp/R from the thermo network, H/RT and G/RT
  * from the polynomials.  MLP_CPH: cp/R and H/RT from the network.  G/RT (the
