@@ -21,16 +21,22 @@ from paper_1905_09395_b300 import (FP64, MIXED, THERMO_MLP, THERMO_POLY, Mechani
 pytestmark = pytest.mark.gpu
 
 MODES = {"fp64": dict(precision=FP64), "mixed": dict(precision=MIXED),
-         "mixed_mlp": dict(precision=MIXED, thermo=THERMO_MLP)}
+         "mixed_mlp": dict(precision=MIXED, thermo=THERMO_MLP),
+         # kernels compiled for each mechanism at run time (NVRTC)
+         "mixed_mlp_spec": dict(precision=MIXED, thermo=THERMO_MLP, specialize=1)}
 
 
 def _mechanisms(mode, **extra):
-    ms = [Mechanism(synth.small_mechanism(), **MODES[mode], **extra),
-          Mechanism(synth.scale_mechanism(), **MODES[mode], **extra)]
-    if MODES[mode].get("thermo", THERMO_POLY) != THERMO_POLY:
+    opts = dict(MODES[mode], **extra)
+    thermo = opts.pop("thermo", THERMO_POLY)
+    ms = [Mechanism(synth.small_mechanism(), **opts), Mechanism(synth.scale_mechanism(), **opts)]
+    if thermo != THERMO_POLY:
         Ts = np.linspace(300.0, 3000.0, 200_000)
         for m in ms:
             m.mlp_train(Ts, epochs=4, batch=4096, lr=2e-3, seed=1)
+            m.set_options(thermo=thermo)
+    if opts.get("specialize"):
+        assert all(m.is_specialized for m in ms)
     return ms
 
 
@@ -59,7 +65,7 @@ def _drain(srv, n, timeout=120.0):
     return got
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_mlp"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_mlp", "mixed_mlp_spec"])
 def test_same_alone_and_in_the_mix(mode):
     ms = _mechanisms(mode)
     reqs = _requests(seed=5, n_req=12)
