@@ -66,7 +66,10 @@ stev_status spec_compile(const SpecKey& k, std::vector<char>* cubin, std::string
   if (nvrtcCreateProgram(&prog, head, "stev_spec.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return fail(STEV_ECUDA, "nvrtcCreateProgram failed");
   const std::string name = kernel_name(k);
-  nvrtcAddNameExpression(prog, name.c_str());
+  if (nvrtcAddNameExpression(prog, name.c_str()) != NVRTC_SUCCESS) {
+    nvrtcDestroyProgram(&prog);
+    return fail(STEV_ECUDA, "nvrtcAddNameExpression(%s) failed", name.c_str());
+  }
   const std::string inc1 = "-I" + csrc_dir(), inc2 = "-I" + cuda_include_dir();
   const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device",
                         "-lineinfo", inc1.c_str(), inc2.c_str()};
@@ -82,13 +85,19 @@ stev_status spec_compile(const SpecKey& k, std::vector<char>* cubin, std::string
                 k.R, nvrtcGetErrorString(rc), lg.c_str());
   }
   const char* low = nullptr;
-  nvrtcGetLoweredName(prog, name.c_str(), &low);
-  if (lowered) *lowered = low ? low : "";
   size_t cb = 0;
-  nvrtcGetCUBINSize(prog, &cb);
+  if (nvrtcGetLoweredName(prog, name.c_str(), &low) != NVRTC_SUCCESS || !low ||
+      nvrtcGetCUBINSize(prog, &cb) != NVRTC_SUCCESS || cb == 0) {
+    nvrtcDestroyProgram(&prog);
+    return fail(STEV_ECUDA, "specialised kernel %s: no lowered name or CUBIN", name.c_str());
+  }
+  if (lowered) *lowered = low;  // copied before the program is destroyed
   if (cubin) {
     cubin->resize(cb);
-    nvrtcGetCUBIN(prog, cubin->data());
+    if (nvrtcGetCUBIN(prog, cubin->data()) != NVRTC_SUCCESS) {
+      nvrtcDestroyProgram(&prog);
+      return fail(STEV_ECUDA, "nvrtcGetCUBIN failed for %s", name.c_str());
+    }
   }
   nvrtcDestroyProgram(&prog);
   return STEV_OK;
@@ -128,10 +137,6 @@ extern "C" stev_status stev_spec_compile_check(int n_species, int n_reactions, i
   std::vector<char> cubin;
   std::string lg;
   const stev_status st = stev::host::spec_compile(k, &cubin, nullptr, &lg);
-  if (log && log_len) {
-    std::snprintf(log, log_len, "%s", lg.c_str());
-  }
-  if (st == STEV_OK && cubin.empty())
-    return stev::host::fail(STEV_ECUDA, "specialised kernel compiled to an empty image");
+  if (log && log_len) std::snprintf(log, log_len, "%s", lg.c_str());
   return st;
 }
