@@ -83,10 +83,10 @@ typedef struct {
                          mechanism and precision (0) */
   int specialize;     /* mixed precision: 1 compiles the solver kernel for this
                          mechanism at run time (NVRTC; its sizes and rate-law
-                         kind as constants, SURVEY's per-mechanism kernels),
-                         a few seconds at creation or when the options change;
-                         0 uses the generic kernel (0).  Needs the csrc
-                         directory beside the library and CUDA's headers. */
+                         kind as constants), about a second at creation or
+                         when the options change; 0 uses the generic kernel
+                         (0).  Needs the csrc directory beside the library and
+                         CUDA's headers. */
 } stev_options;
 
 /* Fills *opt with the defaults above.  Never fails for a non-NULL opt. */
