@@ -193,13 +193,13 @@ static int choose_group(int S, int R, const stev_options& o) {
 }
 
 // Launch configuration of the persistent kernel: as many resident cells per
-// CTA as shared memory holds (whole warps, <= kMaxBlock threads), then as
-// many CTAs as fit on every SM.
+// CTA as shared memory holds (whole warps, <= the block limit), then as many
+// CTAs as fit on every SM.  Atomic: on failure the mechanism keeps its
+// previous configuration and kernel.
 static stev_status configure(stev_mechanism* m) {
   cudaDeviceProp prop;
   CUDA_TRY(cudaGetDeviceProperties(&prop, m->device));
-  m->G = choose_group(m->S, m->R, m->opt);
-  const int G = m->G;
+  const int G = choose_group(m->S, m->R, m->opt);
   const bool mixed = m->opt.precision == STEV_MIXED;
   const size_t tables =
       mixed ? table_smem_bytes_mixed(m->S, m->R, m->n_gather, m->n_hi_bins, m->opt.dft_n, m->general)
@@ -208,7 +208,7 @@ static stev_status configure(stev_mechanism* m) {
   const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n, net)
                             : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
   const size_t limit = prop.sharedMemPerBlockOptin;
-  // the network kernel adds an evaluator warp and per-CTA buffers (sized here
+  // the network kernel adds evaluator warps and per-CTA buffers (sized here
   // for its largest CTA)
   const int max_cells = net ? kMaxBlockMixedNet / 32 - 2 : (mixed ? kMaxBlockMixed : kMaxBlock) / G;
   const size_t extra = net ? net_cta_smem_bytes(max_cells) : 0;
@@ -222,24 +222,59 @@ static stev_status configure(stev_mechanism* m) {
   const int block = cells * G + (net ? 32 * net_evaluators(cells) : 0);
   const void* k = reinterpret_cast<const void*>(select_kernel(m->opt.precision, G, m->opt.thermo,
                                                               m->opt.dft_n));
+  // a kernel compiled for this mechanism: reused if its key is unchanged; a
+  // new one replaces the old only once the whole configuration succeeded
+  cudaLibrary_t new_lib = nullptr;
+  cudaKernel_t new_k = nullptr;
+  const stev::host::SpecKey key{m->S, m->R, m->Rrev, m->general, G, m->opt.dft_n == 13 ? 13 : 0,
+                                net ? 1 : 0};
   if (mixed && m->opt.specialize) {
-    const stev::host::SpecKey key{m->S, m->R, m->Rrev, m->general, G,
-                                  m->opt.dft_n == 13 ? 13 : 0, net ? 1 : 0};
-    if (!m->spec_k || !(key == m->spec_key)) {
-      if (m->spec_lib) cudaLibraryUnload(m->spec_lib);
-      m->spec_lib = nullptr;
-      m->spec_k = nullptr;
-      const stev_status st = stev::host::spec_load(key, &m->spec_lib, &m->spec_k);
+    if (m->spec_k && key == m->spec_key) {
+      k = reinterpret_cast<const void*>(m->spec_k);
+    } else {
+      const stev_status st = stev::host::spec_load(key, &new_lib, &new_k);
       if (st != STEV_OK) return st;
-      m->spec_key = key;
+      k = reinterpret_cast<const void*>(new_k);
     }
-    k = reinterpret_cast<const void*>(m->spec_k);
   }
-  CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto drop_new = [&]() {
+    if (new_lib) cudaLibraryUnload(new_lib);
+  };
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+  if (e != cudaSuccess) {
+    drop_new();
+    return fail(STEV_ECUDA, "configuring the solver kernel: %s", cudaGetErrorString(e));
+  }
+  if (per_sm < 1) {
+    drop_new();
+    return fail(STEV_EINVAL, "persistent kernel cannot be resident");
+  }
+  if (!m->d_counter) {
+    e = cudaMalloc(&m->d_counter, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      drop_new();
+      return fail(STEV_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+  }
+  if (!m->d_net_stalls) {
+    e = cudaMalloc(&m->d_net_stalls, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->d_net_stalls, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      drop_new();
+      return fail(STEV_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+  }
+  // commit
+  if (new_lib) {
+    if (m->spec_lib) cudaLibraryUnload(m->spec_lib);
+    m->spec_lib = new_lib;
+    m->spec_k = new_k;
+    m->spec_key = key;
+  }
   m->kfn = k;
-  if (per_sm < 1) return fail(STEV_EINVAL, "persistent kernel cannot be resident");
+  m->G = G;
   m->block = block;
   m->cells = cells;
   m->per_sm = per_sm;
@@ -247,11 +282,6 @@ static stev_status configure(stev_mechanism* m) {
   m->grid = per_sm * prop.multiProcessorCount;
   m->smem = smem;
   m->nslots = (long long)m->grid * cells;
-  if (!m->d_counter) CUDA_TRY(cudaMalloc(&m->d_counter, sizeof(unsigned long long)));
-  if (!m->d_net_stalls) {
-    CUDA_TRY(cudaMalloc(&m->d_net_stalls, sizeof(unsigned long long)));
-    CUDA_TRY(cudaMemset(m->d_net_stalls, 0, sizeof(unsigned long long)));
-  }
   return STEV_OK;
 }
 
@@ -501,37 +531,59 @@ extern "C" stev_status stev_mechanism_create_orders(
   return STEV_OK;
 }
 
+// The DFT twiddles of the high bins for window N and first high bin n
+// (Eq. 9), in FP64 and FP32.  On failure the mechanism has none (kfn cleared:
+// no solve runs until options are set successfully).
+static stev_status upload_twiddles(stev_mechanism* m, int N, int hi_first) {
+  const int nb = N / 2 - hi_first + 1;
+  std::vector<double> tw((size_t)nb * 2 * N);
+  for (int b = 0; b < nb; ++b) {
+    const int j = hi_first + b;
+    for (int k = 0; k < N; ++k) {
+      const double ang = -2.0 * M_PI * (double)j * (double)k / (double)N;
+      tw[(size_t)b * 2 * N + k] = std::cos(ang);
+      tw[(size_t)b * 2 * N + N + k] = std::sin(ang);
+    }
+  }
+  std::vector<float> twf(tw.begin(), tw.end());
+  CUDA_TRY(cudaDeviceSynchronize());
+  if (m->d_tw) cudaFree(m->d_tw);
+  if (m->d_twf) cudaFree(m->d_twf);
+  m->d_tw = nullptr;
+  m->d_twf = nullptr;
+  cudaError_t e = cudaMalloc(&m->d_tw, tw.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_twf, twf.size() * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_twf, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    m->kfn = nullptr;
+    return fail(STEV_ECUDA, "twiddle table: %s", cudaGetErrorString(e));
+  }
+  m->n_hi_bins = nb;
+  return STEV_OK;
+}
+
+// New options take effect only if the kernel configuration for them
+// succeeds; otherwise the previous options, tables and kernel stay.
 extern "C" stev_status stev_mechanism_set_options(stev_mechanism* m, const stev_options* opt) {
   g_err.clear();
   if (!m || !opt) return fail(STEV_EINVAL, "NULL argument");
   stev_status st = check_options(opt);
   if (st != STEV_OK) return st;
-  if (opt->dft_n != m->opt.dft_n || opt->dft_hi_first != m->opt.dft_hi_first) {
-    // the twiddle table depends on N and n
-    const int nb = opt->dft_n / 2 - opt->dft_hi_first + 1;
-    std::vector<double> tw((size_t)nb * 2 * opt->dft_n);
-    for (int b = 0; b < nb; ++b) {
-      const int j = opt->dft_hi_first + b;
-      for (int k = 0; k < opt->dft_n; ++k) {
-        const double ang = -2.0 * M_PI * (double)j * (double)k / (double)opt->dft_n;
-        tw[(size_t)b * 2 * opt->dft_n + k] = std::cos(ang);
-        tw[(size_t)b * 2 * opt->dft_n + opt->dft_n + k] = std::sin(ang);
-      }
-    }
-    CUDA_TRY(cudaDeviceSynchronize());
-    if (m->d_tw) cudaFree(m->d_tw);
-    m->d_tw = nullptr;
-    CUDA_TRY(cudaMalloc(&m->d_tw, tw.size() * sizeof(double)));
-    CUDA_TRY(cudaMemcpy(m->d_tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice));
-    std::vector<float> twf(tw.begin(), tw.end());
-    if (m->d_twf) cudaFree(m->d_twf);
-    m->d_twf = nullptr;
-    CUDA_TRY(cudaMalloc(&m->d_twf, twf.size() * sizeof(float)));
-    CUDA_TRY(cudaMemcpy(m->d_twf, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice));
-    m->n_hi_bins = nb;
+  const stev_options old = m->opt;
+  const bool tw_change = opt->dft_n != old.dft_n || opt->dft_hi_first != old.dft_hi_first;
+  if (tw_change) {
+    st = upload_twiddles(m, opt->dft_n, opt->dft_hi_first);
+    if (st != STEV_OK) return st;
   }
   m->opt = *opt;
-  return configure(m);
+  st = configure(m);
+  if (st == STEV_OK) return STEV_OK;
+  const std::string msg = g_err;
+  m->opt = old;
+  if (tw_change && upload_twiddles(m, old.dft_n, old.dft_hi_first) != STEV_OK) m->kfn = nullptr;
+  return fail(st, "%s (previous options kept)", msg.c_str());
 }
 
 extern "C" stev_status stev_mechanism_get_options(const stev_mechanism* m, stev_options* opt) {
@@ -627,6 +679,7 @@ static stev_status check_solve_args(stev_mechanism* m, long n, const void* T, co
 // launch configuration chosen by configure().
 static cudaError_t launch_solver(const stev_mechanism* m, int grid, const Launch& L,
                                  cudaStream_t s) {
+  if (!m->kfn) return cudaErrorInvalidDeviceFunction;  // no valid configuration
   Launch arg = L;
   void* args[] = {&arg};
   const cudaError_t e =

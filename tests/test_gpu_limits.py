@@ -89,3 +89,25 @@ def test_long_fluid_step_hits_the_iteration_cap():
     assert (ref[3] == CELL_MAXITER).all() and (gpu[3] == CELL_MAXITER).all()
     assert (gpu[2] == 300).all()
     assert np.abs(gpu[1] - ref[1]).max() <= 1e-9
+
+
+def test_failed_option_change_keeps_the_previous_configuration():
+    # 64/512 in FP64 fits one cell per warp but not four (lanes_per_cell = 8):
+    # the change is refused and the mechanism keeps solving as before
+    from paper_1905_09395_b300 import StevError
+    mech = _max_mech()
+    T, P, Y = synth.make_cells(mech, 8, seed=2, T_range=(1000, 2000), P_atm_range=(1, 3),
+                               dirichlet=0.5)
+    m = Mechanism(mech, max_iters=3)
+    import torch
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (T, P, Y)]
+    before = [x.cpu().numpy() for x in m.solve(*d, 1e-3)]
+    slots = m.resident_slots
+    with pytest.raises(StevError):
+        m.set_options(lanes_per_cell=8, dft_n=9)
+    assert m.options.lanes_per_cell == 0 and m.options.dft_n == 13
+    assert m.resident_slots == slots
+    after = [x.cpu().numpy() for x in m.solve(*d, 1e-3)]
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+    m.close()
