@@ -40,25 +40,26 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
 
   // mixture: sum Y/W and ideal-gas density
   double part = 0.0;
-  for (int i = l; i < S; i += G) part = fma(cY[i], tb.sp[i * SP_STRIDE + SP_INVW], part);
+  for (int i = l; i < S; i += G) part = fma(cY[i], tb.sp[SP_INVW * S + i], part);
   const double sumYW = group_sum<G>(part);
   const double rho = st.P / (kRu * T * sumYW);
 
   // thermo (Eqs. 15-16, G/RT) and gamma-stabilised concentrations (Eqs. 6-7)
   double cpp = 0.0;
   for (int i = l; i < S; i += G) {
-    const double* sp = tb.sp + i * SP_STRIDE;
-    const double* b = sp + (T < sp[SP_TSPLIT] ? SP_LOW : SP_HIGH);
+    const double* sp = tb.sp + i;  // row k of species i at sp[k * S]
+    const double* b = sp + (T < sp[SP_TSPLIT * S] ? SP_LOW : SP_HIGH) * S;
     const double Yi = cY[i];
-    const double cpR = fma(fma(fma(fma(b[B_A4], T, b[B_A3]), T, b[B_A2]), T, b[B_A1]), T, b[B_A0]);
-    const double hp = fma(fma(fma(b[B_H4], T, b[B_H3]), T, b[B_H2]), T, b[B_H1]);
-    cH[i] = fma(hp, T, b[B_A0]) + b[B_A5] * invT;
-    const double gp = fma(fma(fma(b[B_G4], T, b[B_G3]), T, b[B_G2]), T, b[B_H1]);
-    cG[i] = fma(b[B_A0], 1.0 - lnT, fma(b[B_A5], invT, -b[B_A6])) - gp * T;
-    cpp = fma(Yi * cpR, sp[SP_INVW], cpp);
+    const double cpR = fma(fma(fma(fma(b[B_A4 * S], T, b[B_A3 * S]), T, b[B_A2 * S]), T,
+                               b[B_A1 * S]), T, b[B_A0 * S]);
+    const double hp = fma(fma(fma(b[B_H4 * S], T, b[B_H3 * S]), T, b[B_H2 * S]), T, b[B_H1 * S]);
+    cH[i] = fma(hp, T, b[B_A0 * S]) + b[B_A5 * S] * invT;
+    const double gp = fma(fma(fma(b[B_G4 * S], T, b[B_G3 * S]), T, b[B_G2 * S]), T, b[B_H1 * S]);
+    cG[i] = fma(b[B_A0 * S], 1.0 - lnT, fma(b[B_A5 * S], invT, -b[B_A6 * S])) - gp * T;
+    cpp = fma(Yi * cpR, sp[SP_INVW * S], cpp);
     const double y = fmax(Yi, 0.0);
     const double ys = (L.alpha > 0.0) ? y * (y / (L.alpha + y)) : y;
-    cC[i] = rho * ys * sp[SP_INVW];
+    cC[i] = rho * ys * sp[SP_INVW * S];
   }
   const double cpsum = group_sum<G>(cpp);
   __syncwarp();
@@ -122,7 +123,7 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
       const int e = tb.gent[k];
       wd = fma(L.general ? tb.gnu[k] : kNuOf[e & 15], cQ[e >> 4], wd);
     }
-    const double ri = tb.sp[i * SP_STRIDE + SP_W] * wd * invRho;
+    const double ri = tb.sp[SP_W * S + i] * wd * invRho;
     hwp = fma(cH[i], wd, hwp);
     cC[i] = ri;  // concentrations are no longer needed: keep dY/dt here
     const double rstar = fmax(-ri, 1.0e-30);
@@ -216,7 +217,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) stev_fp64_kernel(Launch L) {
   double* s_tw = reinterpret_cast<double*>(s_ri + R);
   int* s_gptr = reinterpret_cast<int*>(s_tw + L.n_hi_bins * 2 * L.dft_n);
   int* s_gent = s_gptr + S + 1;
-  for (int t = threadIdx.x; t < S * SP_STRIDE; t += blockDim.x) s_sp[t] = L.sp_tab[t];
+  // species table transposed to [row][S] in shared memory: lane i reading
+  // species i then walks consecutive banks (species-major rows 256 bytes apart
+  // put every lane on the same bank)
+  for (int t = threadIdx.x; t < S * SP_STRIDE; t += blockDim.x)
+    s_sp[(t % SP_STRIDE) * S + t / SP_STRIDE] = L.sp_tab[t];
   for (int t = threadIdx.x; t < R * RX_STRIDE; t += blockDim.x) s_rx[t] = L.rx_tab[t];
   for (int t = threadIdx.x; t < R; t += blockDim.x) s_ri[t] = L.rx_idx[t];
   for (int t = threadIdx.x; t < L.n_hi_bins * 2 * L.dft_n; t += blockDim.x) s_tw[t] = L.dft_tw[t];
