@@ -287,16 +287,37 @@ def run_reference(args):
     return 0
 
 
+L2_BYTES = 126 << 20
+
+
+def inputs_fit_l2(*arrays) -> bool:
+    return sum(a.nbytes for a in arrays) < L2_BYTES
+
+
+def l2_note(*arrays, flushed: bool = True) -> str:
+    mb = sum(a.nbytes for a in arrays) >> 20
+    if not inputs_fit_l2(*arrays):
+        return "inputs (%d MB) larger than L2" % mb
+    if flushed:
+        return "inputs (%d MB) within L2: a 256 MB buffer is written before each timed solve" % mb
+    return "inputs (%d MB) within L2 (not flushed)" % mb
+
+
 def timed_solves(m, Td, Pd, Yd, dt, out, steps, warmup, warmup_cells, stream, dist=None,
                  sample_clocks=None):
     """W warm-up solves on the first warmup_cells cells (same kernel and launch
     configuration), then K timed solves of every cell, CUDA events on the
-    launching stream, synchronised and barriered on both sides."""
+    launching stream, synchronised and barriered on both sides.  When the
+    inputs fit in L2, a buffer larger than L2 is written (outside the events)
+    before each timed solve."""
     import torch
     nw = min(Td.shape[0], warmup_cells)
     wout = tuple(x[:nw] for x in out)
     for _ in range(warmup):
         m.solve(Td[:nw], Pd[:nw], Yd[:nw], dt, out=wout)
+    flush = None
+    if inputs_fit_l2(Td, Pd, Yd):
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=Td.device)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
@@ -304,6 +325,8 @@ def timed_solves(m, Td, Pd, Yd, dt, out, steps, warmup, warmup_cells, stream, di
     torch.cuda.synchronize()
     t0 = time.time()
     for k in range(steps):
+        if flush is not None:
+            flush.zero_()
         ev[k][0].record(stream)
         m.solve(Td, Pd, Yd, dt, out=out)
         ev[k][1].record(stream)
@@ -361,7 +384,8 @@ def run_uneven(args):
             "config": {"workload": "syn53x325, 64 batches log-uniform 1k-256k cells x %g "
                                    "(%d cells), T0 U[700,2500] K, P U[1,5] atm, Y0 "
                                    "Dirichlet(0.5), dt 5e-4 s" % (args.uneven_scale, total),
-                       "precision": "mixed", "thermo": args.thermo},
+                       "precision": "mixed", "thermo": args.thermo,
+                       "l2": l2_note(*[a for b in host_batches for a in b[:3]], flushed=False)},
             "separate_launches": {"value": total / (ms_sep / 1e3), "ms": ms_sep},
             "cell_steps_per_s": float(iters.sum()) / (ms / 1e3),
             "iters": {"mean": float(iters.mean()), "p50": float(np.percentile(iters, 50)),
@@ -610,9 +634,7 @@ def run_bfer(args):
             "config": {"workload": "bfer: 6 species (CH4 O2 CO H2O CO2 N2), MEPOX + COROX with "
                                    "Table 1 constants, %d cells, T0 U[1200,2200] K, 1 atm, "
                                    "methane-air-like Y0, dt 1e-3 s" % n,
-                       "l2": "inputs (%d MB) %s L2" % ((T.nbytes + P.nbytes + Y.nbytes) >> 20,
-                                                       "larger than" if n >= (1 << 19) else
-                                                       "within")},
+                       "l2": l2_note(T, P, Y)},
             "arms": arms, "gpu_launches": 3 * (args.steps + args.warmup), "clocks": clocks,
             "cpu_baseline": cpu}
     print(json.dumps(line))
@@ -750,8 +772,7 @@ def run_ours(args):
                                   and spec_flag(args) else "generic"),
                        "cells_per_gpu": n, "warmup_cells": nw, "max_iters": extra.get(
                            "max_iters", 200000),
-                       "l2": "inputs (%d MB) larger than L2" % ((T.nbytes + P.nbytes + Y.nbytes)
-                                                                >> 20),
+                       "l2": l2_note(T, P, Y),
                        "parallelism": "dp%d (independent cell batches)" % world},
             "cell_steps_per_s": cell_steps * args.steps / t_max if world == 1 else None,
             "iters": {"mean": float(it_np.mean()), "p50": float(np.percentile(it_np, 50)),
