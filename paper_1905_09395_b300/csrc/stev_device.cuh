@@ -3,6 +3,9 @@
 // Mechanism tables are built once on the host (stev_capi.cu) and staged into
 // shared memory by every CTA of the persistent kernel:
 //   species  : SP_STRIDE doubles each: W, 1/W, T_split, pad, low block, high block
+//              (species-major in global memory; the FP64 kernel stages it
+//              transposed, [row][S], and the mixed kernels use the float
+//              table described at SF_* below, also [row][S])
 //   block    : a0..a6 of NASA-7 plus pre-divided coefficients so that
 //              cp/R = a0 + T(a1 + T(a2 + T(a3 + T a4)))                (Eq. 15)
 //              H/RT = a0 + T(a1/2 + T(a2/3 + T(a3/4 + T a4/5))) + a5/T (Eq. 16)
