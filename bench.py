@@ -37,84 +37,93 @@ METRIC = "cell-solves/s at 1M cells: mixed+MLP vs plain FP64 STEV, 1 B300; p99 l
 UNIT = "cell-solves/s"
 N_CELLS = 1 << 20
 
-# FP64-pipe cost of CUDA's exp() and log() in DFMA-equivalents, measured on
-# B300 by csrc/alu_peaks.cu (dfma 1.667/clk/SM, exp 0.104, log 0.055, div 0.222)
-EXP_OPS, LOG_OPS, DIV_OPS = 16.0, 30.0, 7.5
-# Arithmetic rates per SM and clock measured on B300 by csrc/alu_peaks.cu:
-# DFMA, FFMA, MUFU (ex2.approx) lane operations; the BF16 tensor rate from the
-# measured cuBLAS burst peak (1742.6 TFLOP/s at 2032 MHz).  Peaks are taken at
-# the SM clock sampled during the timed region.
-DFMA_PER_CLK, FFMA_PER_CLK, MUFU_PER_CLK = 1.668, 125.36, 31.66
-BF16_FLOP_PER_CLK = 1742.6e12 / (148 * 2032e6)
+# Rates per SM and clock measured on B300 by csrc/alu_peaks.cu (lane
+# operations): FP64 FMA, CUDA's exp(double), log(double) and FP64 division (all
+# on the FP64 pipe); FP32 FMA; MUFU ex2.approx (the mixed path's exponentials,
+# logarithms and reciprocals).  Peaks are taken at the SM clock sampled during
+# the timed region.
+DFMA_PER_CLK, EXP64_PER_CLK, LOG64_PER_CLK, DIV64_PER_CLK = 1.668, 0.104, 0.055, 0.222
+FFMA_PER_CLK, MUFU_PER_CLK = 125.36, 31.66
 N_SMS = 148
 # DRAM bytes per cell of one launch, from the ncu captures summarised in
-# profiles/ (3,256-, 3,108- and 1,628-cell cases of 300 steps; reads only: the
-# small cases' output writes stay in L2), scaled to the full launch by the
-# cells it processes.  None when the kernel changed after its capture.
+# profiles/ (reads only: the small cases' output writes stay in L2), scaled to
+# the full launch by the cells it processes.  None when the kernel changed
+# after its capture.
 DRAM_BYTES_PER_CELL = {"mixed": 956416 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 939520 / 3108}
 
 
-def fp64_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int) -> float:
-    """Algorithmic FP64 work of one STEV iteration of one cell, in DFMA-equivalents.
-
-    Counted from the method (not from the kernel): per species thermo (cp 4,
-    H/RT 6, G/RT 7 ops), mixture and cp sums (3), gamma and concentration
-    (3 + 1 division), production-rate bookkeeping (dY/dt 2, H.wdot 1),
-    limiter (4 + 1 division amortised by the min), Euler (1); per reaction
-    ln kf (2) + exp, reactant and product products (2), dG (3), ln kr (2) +
-    exp, net rate and rOF (2); one FMA per stoichiometric entry; per
-    reversible reaction the history entry (1), the N-point window sum of
-    Eq. 9's D0 (N-1) and the rOF update (3); per cell-step log T, 1/T and the
-    scalar updates (~12 ops + log + 2 divisions)."""
-    species = S * (4 + 6 + 7 + 3 + 3 + DIV_OPS + 3 + 4 + 1)
-    reactions = R * (2 + 2 + 3 + 2 + 2 + 2 * EXP_OPS)
-    gather = nnz
-    dft = Rrev * (1 + 12 + 3)
-    scalars = 12 + LOG_OPS + 3 * DIV_OPS
-    return species + reactions + gather + dft + scalars
+def bf16_tflops() -> tuple:
+    """The BF16 dense tensor rate for a kernel timed inside a long step: the
+    sustained cuBLAS figure of MEASURED_PEAKS.json, else the profiling
+    fallback (sustained near 1.4 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1400.0, "fallback (sustained)"
 
 
-def mixed_ops_per_cell_step(S: int, R: int, Rrev: int, nnz: int, net: bool = False) -> float:
-    """Algorithmic work of one mixed-precision STEV iteration of one cell, in
-    FP32-FMA-equivalents: the method's operations as counted by
-    fp64_ops_per_cell_step, placed on the mixed plan's units (the composite
-    bound t = flops / peak_fp + exps / peak_mufu + mma_flops / peak_bf16):
-    plain operations on the FP32 pipe; two exponentials per reaction, one
-    reciprocal per species (gamma), the scalar reciprocals and lg2 T on MUFU,
-    weighted by the measured FFMA / MUFU rate ratio; with the thermo network,
-    its per-cell MMA flops (1 x 64 x 64 and 64 x S for cp/R) weighted by the
-    BF16 tensor rate, in place of the cp polynomial."""
-    fma = (S * (4 + 6 + 7 + 3 + 3 + 1 + 3 + 4 + 1) + R * (2 + 2 + 3 + 2 + 2) + nnz +
-           Rrev * (1 + 12 + 3) + 12 + 3)
-    mufu = 2 * R + S + 3 + 1
-    ops = fma + mufu * FFMA_PER_CLK / MUFU_PER_CLK
+def method_counts(S: int, R: int, net: bool = False) -> dict:
+    """The method's work per cell-step (one STEV iteration of one cell), as
+    counted from the algorithm with the sliding DFT: about 40 S + 43 R flops,
+    2 R exponentials (forward and reverse rate constants, Eqs. 28-30), S
+    divisions (gamma, Eqs. 6-7) and 2 logarithms (ln T); with the thermo
+    network (Sec. 3) its MMA flops 2 (64 + 64 x 64 + 64 x 3S) replace about
+    28 S thermo flops."""
+    c = {"flops": 40 * S + 43 * R, "exp": 2 * R, "div": S, "log": 2, "mma": 0}
     if net:
-        ops -= 4 * S
-        ops += 2 * (64 * 64 + 64 * S) / BF16_FLOP_PER_CLK * FFMA_PER_CLK
-    return ops
+        c["flops"] -= 28 * S
+        c["mma"] = 2 * (64 + 64 * 64 + 64 * 3 * S)
+    return c
+
+
+def bound_s_per_cell_step(S: int, R: int, precision: str, net: bool, mhz: float,
+                          bf16: float) -> float:
+    """Composite ALU bound of one cell-step: each class of operation at the
+    measured rate of the unit that executes it, t = flops / peak_fp +
+    exps / peak_exp + divs / peak_div + logs / peak_log + mma / peak_bf16.
+    FP64 path: flops on the FP64 pipe (FMA = 2 flops), exp / log / division
+    at the rates of CUDA's double routines.  Mixed path: flops on the FP32
+    pipe, exponentials, logarithms and reciprocals on MUFU, MMA flops at the
+    BF16 tensor rate (bf16, TFLOP/s)."""
+    clk = N_SMS * mhz * 1e6
+    c = method_counts(S, R, net)
+    if precision == "fp64":
+        return (c["flops"] / (2 * DFMA_PER_CLK * clk) + c["exp"] / (EXP64_PER_CLK * clk) +
+                c["div"] / (DIV64_PER_CLK * clk) + c["log"] / (LOG64_PER_CLK * clk))
+    return (c["flops"] / (2 * FFMA_PER_CLK * clk) +
+            (c["exp"] + c["div"] + c["log"]) / (MUFU_PER_CLK * clk) + c["mma"] / (bf16 * 1e12))
+
+
+def alu_roofline(precision: str, S: int, R: int, net: bool, cell_steps: float, seconds: float,
+                 sm_mhz: float) -> dict:
+    """Composite ALU roofline of a solve: frac = achieved cell-steps/s x the
+    bound time of one cell-step.  Reported as flop rates of the bound pipe
+    (FP64 FMA for the plain path, FP32 FMA for the mixed path): the peak is
+    that pipe's measured rate x SMs x the sampled clock, and a cell-step's
+    flop-equivalents are its bound time x that peak."""
+    mhz = sm_mhz or 2032.0
+    bf16, bf16_src = bf16_tflops()
+    t = bound_s_per_cell_step(S, R, precision, net, mhz, bf16)
+    per_clk = DFMA_PER_CLK if precision == "fp64" else FFMA_PER_CLK
+    peak = 2 * per_clk * N_SMS * mhz * 1e6               # flop/s of the bound pipe
+    rate = cell_steps / seconds
+    return {"bound": "alu", "achieved": rate * t * peak / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": rate * t, "cell_steps_per_s": rate,
+            "cell_steps_per_s_bound": 1.0 / t, "counts_per_cell_step": method_counts(S, R, net),
+            "pipe": ("fp64 (DFMA %.3f, exp %.3f, log %.3f, div %.3f /clk/SM)"
+                     % (DFMA_PER_CLK, EXP64_PER_CLK, LOG64_PER_CLK, DIV64_PER_CLK)
+                     if precision == "fp64" else
+                     "fp32 composite (FFMA %.2f, MUFU %.2f /clk/SM%s)"
+                     % (FFMA_PER_CLK, MUFU_PER_CLK,
+                        ", BF16 %.1f TFLOP/s %s" % (bf16, bf16_src) if net else "")) +
+                    " (csrc/alu_peaks.cu) x %d SMs x %.0f MHz sampled" % (N_SMS, mhz)}
 
 
 def spec_flag(args) -> int:
     """Mixed-precision mechanisms run the kernel compiled for them (NVRTC at
     creation, outside the timed region) unless --generic."""
     return 0 if getattr(args, "generic", False) else 1
-
-
-def alu_roofline(precision: str, ops: float, cell_steps: float, seconds: float,
-                 sm_mhz: float) -> dict:
-    """Composite ALU roofline: achieved = ops x cell-steps / s (FMA = 2 flops),
-    peak = the pipe's measured rate per SM and clock x SMs x the SM clock
-    sampled during the run."""
-    mhz = sm_mhz or 2032.0
-    per_clk = DFMA_PER_CLK if precision == "fp64" else FFMA_PER_CLK
-    peak = per_clk * N_SMS * mhz * 1e6
-    achieved = ops * cell_steps / seconds
-    return {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * peak / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / peak, "ops_per_cell_step": ops,
-            "pipe": ("fp64: DFMA %.3f/clk/SM" % DFMA_PER_CLK if precision == "fp64" else
-                     "fp32 composite: FFMA %.2f/clk/SM, MUFU %.2f/clk/SM as FFMA-equivalents"
-                     % (FFMA_PER_CLK, MUFU_PER_CLK)) +
-                    " (csrc/alu_peaks.cu) x %d SMs x %.0f MHz sampled" % (N_SMS, mhz)}
 
 
 def workload(n_cells: int, rank: int = 0):
@@ -333,7 +342,7 @@ def timed_solves(m, Td, Pd, Yd, dt, out, steps, warmup, warmup_cells, stream, di
     torch.cuda.synchronize()
     wall = time.time() - t0
     barrier(dist)
-    return [a.elapsed_time(b) for a, b in ev], wall, nw
+    return [a.elapsed_time(b) for a, b in ev], wall, nw, (steps if flush is not None else 0)
 
 
 def run_uneven(args):
@@ -484,8 +493,9 @@ def serve_arm(arm, args, trained=None, rate=None, seconds=None, drain=None):
                 break
             wait = 0.005 if k == len(reqs) else min(0.005, max(0.0, reqs[k][0] - now))
             reports += srv.poll(timeout=wait)
-        srv.stop(timeout=120.0)     # cells in flight finish; nothing new starts
-        elapsed = time.perf_counter() - t0
+        t_stop = srv.clock()        # the run's end on the server clock: unfinished
+        srv.stop(timeout=120.0)     # requests are censored here; cells in flight
+        elapsed = time.perf_counter() - t0  # finish, nothing new starts
         while True:
             more = srv.poll()
             if not more:
@@ -498,6 +508,19 @@ def serve_arm(arm, args, trained=None, rate=None, seconds=None, drain=None):
     done = [d for d in reports if d["status"] == 0]
     lat = np.array([d["t_done"] - d["t_submit"] for d in done]) if done else np.zeros(0)
     pct = lambda q: float(np.percentile(lat, q)) if len(lat) else None
+    # every offered request's latency, an unfinished one counted as censored at
+    # the run's end (a lower bound on its latency); queue wait (submit to
+    # admission) and service time (admission to results) of the requests that
+    # reached them
+    seen = {d["id"] for d in reports}
+    cens = [t_stop - d["t_submit"] for d in reports if d["status"] != 0]
+    cens += [t_stop - (c0 + reqs[j][0]) for j in range(len(reqs) - len(seen))]
+    lat_all = np.concatenate([lat, np.array(cens, dtype=np.float64)])
+    admitted_t = [d for d in reports if d["t_admit"] > 0]
+    qwait = np.array([d["t_admit"] - d["t_submit"] for d in admitted_t] +
+                     [t_stop - d["t_submit"] for d in reports if d["t_admit"] <= 0])
+    service = np.array([d["t_done"] - d["t_admit"] for d in done])
+    q = lambda a, p: float(np.percentile(a, p)) if len(a) else None
     cells = sum(d["cells_done"] for d in reports)
     by = {}
     for i, t in enumerate(tabs):
@@ -520,8 +543,14 @@ def serve_arm(arm, args, trained=None, rate=None, seconds=None, drain=None):
             "offered_cells_per_s": sum(r[2] for r in reqs) / seconds,
             "completed_requests": len(done),
             "completed_cells": int(sum(d["n_cells"] for d in done)), "cells_solved": int(cells),
-            "latency_p50_s": pct(50), "latency_p99_s": pct(99),
+            "latency_p50_s": q(lat_all, 50), "latency_p99_s": q(lat_all, 99),
+            "latency_note": "over every offered request; an unfinished one counts as censored "
+                            "at the run's end (a lower bound on its latency)",
+            "censored_requests": int(len(cens)),
+            "finished_latency_p50_s": pct(50), "finished_latency_p99_s": pct(99),
             "latency_max_s": float(lat.max()) if len(lat) else None,
+            "queue_wait_p50_s": q(qwait, 50), "queue_wait_p99_s": q(qwait, 99),
+            "service_p50_s": q(service, 50), "service_p99_s": q(service, 99),
             "backlog_requests": int(len(reqs) - len(done)),
             "submit_lag_max_s": lag, "peak_resident_gb": st["peak_resident_bytes"] / 2**30,
             "kernel_launches": int(st["kernel_launches"]),
@@ -588,6 +617,7 @@ def run_bfer(args):
            torch.empty(n, dtype=torch.uint8, device=dev))
     stream = torch.cuda.current_stream(dev)
     arms = {}
+    flushes = 0
     with ClockSampler(0) as clk:
         for name, kw in (("mixed+mlp", dict(precision=binding.MIXED, specialize=spec_flag(args))),
                          ("mixed_poly", dict(precision=binding.MIXED, specialize=spec_flag(args))),
@@ -600,8 +630,9 @@ def run_bfer(args):
                 hist = m.mlp_train(Ts, epochs=args.mlp_epochs, batch=4096, lr=2e-3, seed=7)
                 m.set_options(thermo=binding.THERMO_MLP)
                 info = {"final_loss": float(hist[-1]), "train_s": time.time() - t0}
-            ms, _, _ = timed_solves(m, Td, Pd, Yd, 1e-3, out, args.steps, args.warmup,
-                                    args.warmup_cells, stream)
+            ms, _, _, nflush = timed_solves(m, Td, Pd, Yd, 1e-3, out, args.steps, args.warmup,
+                                            args.warmup_cells, stream)
+            flushes += nflush
             it = out[2].cpu().numpy().astype(np.int64)
             st = np.bincount(out[3].cpu().numpy(), minlength=4)
             arms[name] = {"value": n / (float(np.mean(ms)) / 1e3), "unit": UNIT,
@@ -635,7 +666,8 @@ def run_bfer(args):
                                    "Table 1 constants, %d cells, T0 U[1200,2200] K, 1 atm, "
                                    "methane-air-like Y0, dt 1e-3 s" % n,
                        "l2": l2_note(T, P, Y)},
-            "arms": arms, "gpu_launches": 3 * (args.steps + args.warmup), "clocks": clocks,
+            "arms": arms, "gpu_launches": 3 * args.steps,
+            "other_launches_in_timed_region": {"l2_flush": flushes}, "clocks": clocks,
             "cpu_baseline": cpu}
     print(json.dumps(line))
     return 0
@@ -651,7 +683,6 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     mech, T, P, Y, dt = workload(args.cells, rank)
     S, R = mech.n_species, mech.n_reactions
-    Rrev, nnz = int(mech.reversible.sum()), len(mech.rxn_species)
     extra = {} if args.max_iters is None else {"max_iters": args.max_iters}
     prec = binding.MIXED if args.precision == "mixed" else binding.FP64
     m = Mechanism(mech, precision=prec, specialize=spec_flag(args) if prec == binding.MIXED else 0,
@@ -676,8 +707,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     with ClockSampler(local) as clk:
-        ms, wall, nw = timed_solves(m, Td, Pd, Yd, dt, out, args.steps, args.warmup,
-                                    args.warmup_cells, stream, dist)
+        ms, wall, nw, nflush = timed_solves(m, Td, Pd, Yd, dt, out, args.steps, args.warmup,
+                                            args.warmup_cells, stream, dist)
     dev_s = sum(ms) / 1e3
     it_np = out[2].cpu().numpy()
     cell_steps = int(it_np.astype(np.int64).sum())
@@ -711,10 +742,10 @@ def run_ours(args):
 
     clocks = clk.summary()
 
-    def one_solve(mc, precision, ops):
+    def one_solve(mc, precision, net):
         """One timed solve of the same cells by another configuration."""
         with ClockSampler(local) as ck:
-            msx, _, _ = timed_solves(mc, Td, Pd, Yd, dt, out, 1, args.warmup, args.warmup_cells,
+            msx, _, _, _ = timed_solves(mc, Td, Pd, Yd, dt, out, 1, args.warmup, args.warmup_cells,
                                      stream, dist)
         itx = out[2].cpu().numpy().astype(np.int64)
         tx = max_over_ranks(dist, msx[0] / 1e3, dev)
@@ -722,7 +753,7 @@ def run_ours(args):
         return {"value": whole_job_rate(dist, msx[0] / 1e3, n, dev), "unit": UNIT,
                 "ms_per_step": tx * 1e3, "steps": 1,
                 "warmup": args.warmup, "cell_steps_per_s": int(itx.sum()) / tx,
-                "roofline": dict(alu_roofline(precision, ops, int(itx.sum()), msx[0] / 1e3,
+                "roofline": dict(alu_roofline(precision, S, R, net, int(itx.sum()), msx[0] / 1e3,
                                               ckx["sm_mhz"]), traffic=None),
                 "clocks": ckx}
 
@@ -731,33 +762,24 @@ def run_ours(args):
     mixed_poly, plain = None, None
     if args.precision == "mixed" and args.thermo == "mlp" and not args.no_poly_compare:
         mp = Mechanism(mech, precision=binding.MIXED, specialize=spec_flag(args), **extra)
-        mixed_poly = one_solve(mp, "mixed", mixed_ops_per_cell_step(S, R, Rrev, nnz))
+        mixed_poly = one_solve(mp, "mixed", False)
         mp.close()
     if args.precision == "mixed" and not args.no_fp64_compare:
         mf = Mechanism(mech, precision=binding.FP64, **extra)
-        plain = one_solve(mf, "fp64", fp64_ops_per_cell_step(S, R, Rrev, nnz))
+        plain = one_solve(mf, "fp64", False)
         plain_head = [x[:4096].cpu().numpy() for x in out]
         mf.close()
 
     if rank != 0:
         return 0
-    if args.precision == "mixed":
-        ops = mixed_ops_per_cell_step(S, R, Rrev, nnz, net=args.thermo == "mlp")
-        ops_note = ("the method's operations on the mixed plan's units (FP32 pipe; exps, "
-                    "reciprocals and lg2 T on MUFU%s), in FFMA-equivalents"
-                    % ("; the network's MMA flops on the BF16 tensor rate"
-                       if args.thermo == "mlp" else ""))
-    else:
-        ops = fp64_ops_per_cell_step(S, R, Rrev, nnz)
-        ops_note = ("the method's FP64 work: exp = %g, log = %g, div = %g DFMA-equivalents, "
-                    "measured" % (EXP_OPS, LOG_OPS, DIV_OPS))
-    bpc = DRAM_BYTES_PER_CELL.get(args.precision + ("+mlp" if args.thermo == "mlp" else ""))
-    roofline = alu_roofline(args.precision, ops, cell_steps, float(np.mean(ms)) / 1e3,
+    net = args.precision == "mixed" and args.thermo == "mlp"
+    bpc = DRAM_BYTES_PER_CELL.get(args.precision + ("+mlp" if net else ""))
+    roofline = alu_roofline(args.precision, S, R, net, cell_steps, float(np.mean(ms)) / 1e3,
                             clocks["sm_mhz"])
     roofline.update({"traffic": None if bpc is None else bpc * n,
                      "traffic_note": "DRAM bytes per launch scaled from the ncu capture in "
                                      "profiles/ by the cells processed",
-                     "ops_counted": ops_note, "cell_steps_per_launch": cell_steps})
+                     "cell_steps_per_launch": cell_steps})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -779,22 +801,37 @@ def run_ours(args):
                       "p99": float(np.percentile(it_np, 99)), "max": int(it_np.max())},
             "cell_status": {"ok": int(status[0]), "maxiter": int(status[1]),
                             "nonfinite": int(status[2]), "trange": int(status[3])},
-            "roofline": roofline, "gpu_launches": args.steps, "e2e": e2e,
+            "roofline": roofline, "gpu_launches": args.steps,
+            "other_launches_in_timed_region": {"l2_flush": nflush}, "e2e": e2e,
             "mixed_poly": mixed_poly, "plain_fp64": plain, "thermo_net": mlp_info,
             "wall_s_timed": wall}
     line["clocks"] = clocks
     if world == 1 and not args.no_serve and args.precision == "mixed" and args.thermo == "mlp":
         # p50/p99 latency under the serving load (the scale mechanism's network reused)
+        keys = ("value", "unit", "rate_req_per_s", "arrival_window_s", "elapsed_s",
+                "offered_cells_per_s", "completed_requests", "offered_requests", "cells_solved",
+                "latency_p50_s", "latency_p99_s", "latency_note", "censored_requests",
+                "finished_latency_p50_s", "finished_latency_p99_s", "latency_max_s",
+                "queue_wait_p50_s", "queue_wait_p99_s", "service_p50_s", "service_p99_s",
+                "by_mechanism", "clocks")
         sv = serve_arm("mixed+mlp", args, trained=[None, trained_scale])
-        line["serving"] = {k: sv[k] for k in (
-            "value", "unit", "rate_req_per_s", "arrival_window_s", "elapsed_s",
-            "offered_cells_per_s", "completed_requests", "offered_requests", "cells_solved",
-            "latency_p50_s", "latency_p99_s", "latency_max_s", "by_mechanism", "clocks")}
+        line["serving"] = {k: sv[k] for k in keys}
         line["serving"]["workload"] = ("Poisson %g req/s for %g s (+%g s), sizes log-uniform "
                                        "1k-512k, syn8x20 and syn32x150 half and half, 40 GB "
                                        "budget, host to host" % (args.serve_rate,
                                                                  args.serve_seconds,
                                                                  args.serve_drain))
+        if args.serve_light_seconds > 0:
+            # the same stream at half the cell rate the server reached above
+            # (a load it sustains), as requests per second of the mean size
+            lam = 0.5 * sv["value"] / (sv["offered_cells_per_s"] / args.serve_rate)
+            lt = serve_arm("mixed+mlp", args, trained=[None, trained_scale], rate=lam,
+                           seconds=args.serve_light_seconds, drain=args.serve_light_seconds)
+            line["serving_sustainable"] = {k: lt[k] for k in keys}
+            line["serving_sustainable"]["workload"] = (
+                "Poisson %.3f req/s (half the measured capacity) for %g s (+%g s), same sizes "
+                "and mechanisms, 40 GB budget, host to host"
+                % (lam, args.serve_light_seconds, args.serve_light_seconds))
     if world == 1 and not args.no_cpu_baseline:
         keep = {}
         line["cpu_baseline"] = cpu_baseline(mech, T, P, Y, dt, keep=keep, **extra)
@@ -821,7 +858,7 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window")
     ap.add_argument("--serve-drain", type=float, default=5.0,
                     help="seconds after the last arrival before unfinished requests are cancelled")
-    ap.add_argument("--serve-light-seconds", type=float, default=60.0,
+    ap.add_argument("--serve-light-seconds", type=float, default=30.0,
                     help="serve workload: arrival window of the run at half the measured "
                          "mixed+MLP capacity (0 skips it)")
     ap.add_argument("--no-serve", action="store_true",

@@ -197,7 +197,10 @@ stev_status stev_solve_host(stev_mechanism *mech, long n_cells, const double *T,
  *   are rejected with STEV_EINVAL and a message giving the largest n that
  *   fits (about 31,000 cells at S = 32).
  *   The first call on a device looks up the array's device address (a one-off
- *   set-up); make that first call before any stream capture.
+ *   set-up); make that first call before any stream capture.  The address is
+ *   kept for the life of the process: like every mechanism's device buffers,
+ *   it is invalid after cudaDeviceReset, so do not call this entry point on a
+ *   device after resetting it.
  *   The array keeps the previous call's contents; the work counter is cleared
  *   on every call.  Calls whose GPU work overlaps (different streams, host
  *   threads) race on the array: serialise them.

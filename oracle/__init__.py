@@ -270,7 +270,7 @@ def solve(mech, T, P, Y, dt: float, n_threads: Optional[int] = None,
 
 
 def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] = None,
-                 level: str = "fp64", **opts):
+                 level: str = "fp64", per_run: Optional[dict] = None, **opts):
     """Per-cell spread of the final state under rounding-size rate changes.
 
     Returns (base_result, dY_spread[cells], dT_spread[cells]): the largest
@@ -284,7 +284,9 @@ def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] =
     Y_step^max and the ringing tolerances by 2^-22; for mechanisms with real
     reaction orders also every power C^a by 4 ulp ("fp64") or 2^-17
     ("fp32").  A cell whose spread is far below a tolerance is
-    well-conditioned at that tolerance."""
+    well-conditioned at that tolerance.  per_run (a dict), if given,
+    receives each probe run's own per-cell |change| of Y and T under the run's
+    name."""
     if base is None:
         base = solve(mech, T, P, Y, dt, n_threads=n_threads, **opts)
     dY = np.zeros(len(T))
@@ -302,6 +304,12 @@ def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] =
         kw = dict(opts)
         kw.update(extra)
         r = solve(mech, T, P, Y, dt, n_threads=n_threads, **kw)
-        dY = np.maximum(dY, np.abs(r[1] - base[1]).max(axis=1))
-        dT = np.maximum(dT, np.abs(r[0] - base[0]))
+        eY = np.abs(r[1] - base[1]).max(axis=1)
+        eT = np.abs(r[0] - base[0])
+        dY = np.maximum(dY, eY)
+        dT = np.maximum(dT, eT)
+        if per_run is not None:
+            name = extra.get("probe") or "%s%+.0e" % next(
+                (k, v) for k, v in extra.items() if k != "probe")
+            per_run[name] = (eY, eT)
     return base, dY, dT

@@ -241,7 +241,11 @@ static stev_status configure(stev_mechanism* m) {
     if (new_lib) cudaLibraryUnload(new_lib);
   };
   int per_sm = 0;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // The attribute belongs to the kernel function, which mechanisms with the
+  // same precision, lane group and thermo share: set it to the device's cap
+  // (a ceiling, not a reservation), so that configuring a smaller mechanism
+  // never lowers it below what an earlier, larger one launches with.
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
   if (e != cudaSuccess) {
     drop_new();
@@ -872,6 +876,11 @@ static std::mutex g_noalloc_mutex;
 
 static size_t noalloc_align(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Cells the array could hold if nothing were padded: 16 S + 21 bytes per cell
+// (T, P, T_out: 8 each; Y, Y_out: 8 S each; iters 4; status 1).  Any n above
+// it is rejected before noalloc_bytes() multiplies (no size_t wrap-around).
+static long noalloc_cell_bound(int S) { return (long)(kNoAllocBytes / (16 * (size_t)S + 21)); }
+
 static size_t noalloc_bytes(long n, int S) {
   const size_t nn = (size_t)n;
   return noalloc_align(sizeof(unsigned long long)) + 2 * noalloc_align(nn * 8) +
@@ -892,16 +901,16 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
     return fail(STEV_EINVAL, "NULL array");
   if (m->opt.thermo != STEV_THERMO_POLY && !m->mlp_ready)
     return fail(STEV_EINVAL, "thermo = MLP needs a trained network (stev_mlp_train or stev_mlp_set_params)");
-  if (noalloc_bytes(n, m->S) > kNoAllocBytes) {
-    long lo = 0, hi = n;  // noalloc_bytes(lo) fits, noalloc_bytes(hi) does not
+  if (n > noalloc_cell_bound(m->S) || noalloc_bytes(n, m->S) > kNoAllocBytes) {
+    long lo = 0, hi = std::min(n, noalloc_cell_bound(m->S) + 1);  // lo fits, hi does not
     while (hi - lo > 1) {
       const long mid = (lo + hi) / 2;
       if (noalloc_bytes(mid, m->S) <= kNoAllocBytes) lo = mid; else hi = mid;
     }
     return fail(STEV_EINVAL,
-                "stev_solve_host_noalloc: %ld cells of %d species need %zu bytes of staging; "
-                "its fixed device array holds %zu bytes (at most %ld cells)",
-                n, m->S, noalloc_bytes(n, m->S), kNoAllocBytes, lo);
+                "stev_solve_host_noalloc: %ld cells of %d species need more than the %zu bytes "
+                "of staging its fixed device array holds (at most %ld cells)",
+                n, m->S, kNoAllocBytes, lo);
   }
   int dev = -1;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -910,7 +919,8 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
   unsigned char* base = nullptr;
   {
     // set-up, once per device: the array's device address (host code only
-    // knows a stand-in for it)
+    // knows a stand-in for it).  Like the mechanisms' own device buffers, the
+    // cached address does not outlive the device's context (cudaDeviceReset).
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_ptr[dev]) {
       void* p = nullptr;

@@ -22,7 +22,7 @@
 //         MUFU unit in base 2: k = 2^(log2 k)), rates of progress and rOF
 //         (Eq. 14), production rates, dT/dt, the limiter (Eqs. 1-5) and the
 //         ringing history and DFT test (Eqs. 8-13).
-// B300's FP64 pipe runs at 1/64 of the FP32 rate, and a warp's FP64
+// B300's FP64 pipe runs at 1/75 of the FP32 rate, and a warp's FP64
 // instruction costs it the same time whatever the number of active lanes, so
 // per-cell scalars in FP64 (one cell per warp) would cost 32 lanes' worth.
 #pragma once

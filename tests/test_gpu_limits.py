@@ -111,3 +111,32 @@ def test_failed_option_change_keeps_the_previous_configuration():
     for a, b in zip(before, after):
         np.testing.assert_array_equal(a, b)
     m.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_larger_mechanism_still_launches_after_a_smaller_one_on_the_same_kernel(precision):
+    """Mechanisms with the same precision, lane group and thermo share one
+    kernel function, and its dynamic shared-memory limit is a property of that
+    function.  Configuring a smaller mechanism after a larger one must not
+    leave the larger one unable to launch: the 32/150 mechanism is created
+    first, then the 8/20 one with 32-lane groups (the same kernel instance,
+    fewer bytes of shared memory), and both solve step prefixes that match the
+    oracle."""
+    big = synth.scale_mechanism()
+    small = synth.small_mechanism()
+    Tb, Pb, Yb = synth.make_cells(big, 64, seed=3, T_range=(1000, 2000), P_atm_range=(1, 3),
+                                  dirichlet=0.5)
+    _, Ts, Ps, Ys, dt = synth.small_case(64)
+    import torch
+    mb = Mechanism(big, precision=precision, max_iters=3)
+    ms = Mechanism(small, precision=precision, max_iters=3, lanes_per_cell=32)
+    tol = PREFIX_Y if precision == FP64 else 1e-5
+    for m, mech, (T, P, Y) in ((mb, big, (Tb, Pb, Yb)), (ms, small, (Ts, Ps, Ys)),
+                               (mb, big, (Tb, Pb, Yb))):
+        d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (T, P, Y)]
+        gpu = [x.cpu().numpy() for x in m.solve(*d, 1e-3)]
+        ref = oracle.solve(mech, T, P, Y, 1e-3, max_iters=3)
+        assert (gpu[2] == ref[2]).all() and (gpu[3] == ref[3]).all()
+        assert np.abs(gpu[1] - ref[1]).max() <= tol
+    mb.close()
+    ms.close()

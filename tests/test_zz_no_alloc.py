@@ -62,3 +62,22 @@ def test_noalloc_rejects_oversized_batches():
     msg = L.stev_last_error().decode()
     assert "at most" in msg and "16777216" in msg
     m.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_rejects_a_cell_count_whose_byte_count_would_wrap():
+    """A cell count so large that its byte count would overflow size_t is
+    rejected on the host before any size is computed or any copy is queued
+    (the arrays passed are tiny: nothing may read them)."""
+    L = lib()
+    mech, T, P, Y, dt = synth.small_case(8)
+    m = Mechanism(mech)
+    n = (1 << 62) // 8
+    To, Yo = np.empty(8), np.empty((8, Y.shape[1]))
+    it, st = np.empty(8, np.int32), np.empty(8, np.uint8)
+    code = L.stev_solve_host_noalloc(m._h, n, T.ctypes.data, P.ctypes.data, Y.ctypes.data,
+                                     float(dt), To.ctypes.data, Yo.ctypes.data, it.ctypes.data,
+                                     st.ctypes.data, None)
+    assert code == binding.STEV_EINVAL
+    assert "at most" in L.stev_last_error().decode()
+    m.close()
