@@ -309,7 +309,9 @@ def conditioning(mech, T, P, Y, dt: float, base=None, n_threads: Optional[int] =
         dY = np.maximum(dY, eY)
         dT = np.maximum(dT, eT)
         if per_run is not None:
-            name = extra.get("probe") or "%s%+.0e" % next(
-                (k, v) for k, v in extra.items() if k != "probe")
+            name = extra.get("probe")
+            if name is None:
+                opt, v = next(iter(extra.items()))
+                name = opt + ("_up" if v > opts.get(opt, DEFAULT_OPTS[opt]) else "_down")
             per_run[name] = (eY, eT)
     return base, dY, dT
