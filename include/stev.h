@@ -231,7 +231,8 @@ long stev_mlp_num_params(const stev_mechanism *mech);
  * over 64-sample tiles in a fixed order, so the same inputs train the same
  * network bit for bit.  loss_per_epoch (host, nullable) receives each epoch's
  * mean squared error in standardised units.  Afterwards inference uses BF16
- * copies of W2, W3.  Synchronous. */
+ * copies of W2, W3 (BF16 tensor-core MMAs with FP32 accumulation, inside the
+ * solver step for the cells of each warp).  Synchronous. */
 stev_status stev_mlp_train(stev_mechanism *mech, const double *T_samples, long n_samples,
                            int epochs, int batch, float lr, unsigned long long seed,
                            float *loss_per_epoch);
@@ -239,12 +240,15 @@ stev_status stev_mlp_train(stev_mechanism *mech, const double *T_samples, long n
 /* Trains the network with Levenberg-Marquardt, the optimizer Sec. 3 uses:
  * each iteration takes the next `batch` samples (consecutive windows of the
  * HOST sample array), forms the Jacobian J of the batch's standardised
- * outputs with respect to every parameter (the library's kernel, FP32) and
- * the residuals r, then J^T J and J^T r (cuBLAS, FP32), and solves
- * (J^T J + lambda diag(J^T J) + 1e-12 I) d = J^T r by Cholesky (cuSOLVER,
- * FP64).  The step p - d is kept if it lowers the batch's mean squared error
- * (then lambda /= 3), else lambda *= 2 and the solve is repeated, at most 8
- * times (lambda *= 4 when the matrix is not positive definite).  init: 0 =
+ * outputs with respect to every parameter (FP32, stored transposed) and the
+ * residuals r, then J^T J (stev_gram_tf32: TF32 tensor-core products, FP32
+ * accumulation) and J^T r (FP32), and solves
+ * (J^T J + lambda diag(J^T J) + 1e-12 I) d = J^T r by Jacobi-preconditioned
+ * conjugate gradients (stev_damped_cg: until the residual has fallen by 1e-3
+ * or 400 steps, an inexact Levenberg-Marquardt step); every step runs in the
+ * library's own kernels.  The step p - d is kept if it lowers the batch's mean
+ * squared error (then lambda /= 3), else lambda *= 2 and the solve is
+ * repeated, at most 8 times.  init: 0 =
  * Xavier-uniform weights from splitmix64(seed) and fresh output statistics;
  * 1 = continue from the current network and its statistics (e.g. after
  * stev_mlp_train).  lambda0 > 0: the starting damping.  loss_per_iter
@@ -261,6 +265,33 @@ stev_status stev_mlp_train_lm(stev_mechanism *mech, const double *T_samples, lon
  * Synchronous. */
 stev_status stev_mlp_jacobian(stev_mechanism *mech, const float *params, const double *T,
                               long n, float *J);
+
+/* ---- the Levenberg-Marquardt trainer's linear algebra (Sec. 3), on the
+ * library's own kernels.  DEVICE pointers; synchronous (the stream is
+ * synchronised before returning). */
+
+/* G = X X^T for X [n][ldx] row-major FP32 (the first k values of each row
+ * used): n x n, full (both triangles), row stride ldg >= n.  The products are
+ * taken on the tensor cores in TF32 (inputs rounded to 10-bit mantissas, as
+ * the hardware's TF32 mode does) and accumulated in FP32 (the Gauss-Newton
+ * matrix of the trainer; a 128 x 128 tile per CTA, operands staged by TMA).
+ * X must be 16-byte aligned, ldx >= k a multiple of 4.  STEV_EINVAL on bad
+ * sizes; STEV_ETIMEOUT if a wait of the kernel's pipeline ran out (never
+ * expected; the kernel then stops and G is incomplete). */
+stev_status stev_gram_tf32(long n, long k, const float *X, long ldx, float *G, long ldg,
+                           void *cuda_stream);
+
+/* Solves (A + lambda diag(A) + eps I) x = b for symmetric A [n][lda] (FP32,
+ * row-major, both triangles) by conjugate gradients with the Jacobi
+ * preconditioner diag(A)(1 + lambda) + eps: from x = 0 until the residual
+ * norm has fallen by rtol, or max_iters steps, or a direction of non-positive
+ * curvature (then the current x is returned).  *iters (HOST, nullable)
+ * receives the steps taken.  Dot products are reduced in FP64 in a fixed
+ * order (the same inputs give the same x).  Work arrays are allocated and
+ * freed inside. */
+stev_status stev_damped_cg(long n, const float *A, long lda, const float *b, double lambda,
+                           double eps, float *x, int max_iters, double rtol, int *iters,
+                           void *cuda_stream);
 
 /* Sets / reads the network parameters (HOST arrays) and the per-output mean and
  * standard deviation ([3S] each) used to undo the standardisation. */
@@ -368,9 +399,10 @@ stev_status stev_server_stop(stev_server *srv, double timeout_s);
  * device buffers are not freed.  NULL is a no-op. */
 stev_status stev_server_destroy(stev_server *srv, double timeout_s);
 
-/* Cell-steps of this mechanism's network solves so far that took the
- * polynomials because the network's answer did not arrive within the step's
- * bounded wait (about 2^20 sleeps; never expected).  Synchronous; -1 if the
+/* Cell-steps of this mechanism's network solves that took the polynomials
+ * because the network's answer did not arrive in time.  Each warp now
+ * evaluates the network for its own cells inside the step (no wait), so this
+ * stays 0; kept for callers of earlier versions.  Synchronous; -1 if the
  * device read fails. */
 long long stev_mlp_stalls(const stev_mechanism *mech);
 
@@ -384,7 +416,8 @@ int stev_is_specialized(const stev_mechanism *mech);
 
 /* Compiles (NVRTC, for sm_103a) the mixed-precision kernel specialised for
  * these sizes without loading it: no GPU is needed.  general: real orders or
- * stoichiometry; lanes_per_cell: 8, 16 or 32 (32 with network = 1); dft_n:
+ * stoichiometry; lanes_per_cell: 8, 16 or 32 (network: 1 for the kernel with
+ * the thermo network, any lane group); dft_n:
  * 13 selects the unrolled window, any other value the run-time one.  NVRTC's
  * log is copied into log[log_len] (may be NULL).  STEV_EINVAL for sizes out
  * of range, STEV_ECUDA if the compilation fails (its log in

@@ -32,7 +32,7 @@ EXPORTS = (
     "stev_server_create", "stev_server_submit", "stev_server_poll", "stev_server_get_stats",
     "stev_server_clock", "stev_server_stop", "stev_server_destroy", "stev_mlp_stalls",
     "stev_mlp_train_lm", "stev_mlp_jacobian", "stev_mechanism_create_orders",
-    "stev_is_specialized", "stev_spec_compile_check",
+    "stev_is_specialized", "stev_spec_compile_check", "stev_gram_tf32", "stev_damped_cg",
 )
 
 
@@ -108,6 +108,11 @@ def lib():
         L.stev_mlp_train_lm.restype = I
         L.stev_mlp_jacobian.argtypes = [P, P, P, LNG, P]
         L.stev_mlp_jacobian.restype = I
+        L.stev_gram_tf32.argtypes = [LNG, LNG, P, LNG, P, LNG, P]
+        L.stev_gram_tf32.restype = I
+        L.stev_damped_cg.argtypes = [LNG, P, LNG, P, ctypes.c_double, ctypes.c_double, P,
+                                     I, ctypes.c_double, P, P]
+        L.stev_damped_cg.restype = I
         L.stev_mlp_set_params.argtypes = [P, P, LNG, P, P]
         L.stev_mlp_set_params.restype = I
         L.stev_mlp_get_params.argtypes = [P, P, LNG, P, P]
@@ -474,6 +479,32 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def gram_tf32(X, k: Optional[int] = None, stream=None):
+    """G = X X^T (stev_gram_tf32) for a CUDA float32 tensor X [n][ldx] (the
+    first k columns; ldx a multiple of 4): TF32 tensor-core products, FP32
+    accumulation.  Returns G [n][n] (torch, on X's device)."""
+    import torch
+    n, ldx = int(X.shape[0]), int(X.shape[1])
+    k = ldx if k is None else int(k)
+    G = torch.empty((n, n), dtype=torch.float32, device=X.device)
+    _check(lib().stev_gram_tf32(n, k, X.data_ptr(), ldx, G.data_ptr(), n, _stream_handle(stream)))
+    return G
+
+
+def damped_cg(A, b, lam: float = 0.0, eps: float = 0.0, max_iters: int = 1000,
+              rtol: float = 1e-6, stream=None):
+    """Solves (A + lam diag(A) + eps I) x = b (stev_damped_cg) for CUDA float32
+    tensors A [n][n] (symmetric) and b [n]; returns (x, iterations)."""
+    import torch
+    n = int(A.shape[0])
+    x = torch.empty(n, dtype=torch.float32, device=A.device)
+    it = ctypes.c_int(0)
+    _check(lib().stev_damped_cg(n, A.data_ptr(), int(A.stride(0)), b.data_ptr(), float(lam),
+                                float(eps), x.data_ptr(), int(max_iters), float(rtol),
+                                ctypes.byref(it), _stream_handle(stream)))
+    return x, it.value
 
 
 def spec_compile_check(n_species: int, n_reactions: int, n_reversible: int, general: bool = False,

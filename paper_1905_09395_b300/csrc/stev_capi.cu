@@ -10,9 +10,7 @@
 #include <string>
 #include <vector>
 
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 
 #include "../../include/stev.h"
 #include "stev_device.cuh"
@@ -96,6 +94,7 @@ struct stev_mechanism {
   __nv_bfloat16* d_mlp_W2 = nullptr;      // [64][64]
   __nv_bfloat16* d_mlp_W3 = nullptr;      // [out_pad][64]
   float* d_mlp_misc = nullptr;            // W1, b1, b2 [64 each], b3, mean, std [out_pad each]
+  unsigned char* d_mlp_frag = nullptr;    // the network in MMA fragment order (MlpFrag)
   bool mlp_ready = false;
   // the solver kernel: the generic instantiation, or one compiled for this
   // mechanism (options.specialize)
@@ -151,6 +150,7 @@ static stev_status check_options(const stev_options* o) {
 static void free_mech(stev_mechanism* m) {
   void* ptrs[] = {m->d_sp, m->d_rx, m->d_ri, m->d_rim, m->d_gptr, m->d_gent, m->d_tw, m->d_spf, m->d_rxf,
                   m->d_twf, m->d_counter, m->d_mlp_params, m->d_mlp_W2, m->d_mlp_W3, m->d_mlp_misc,
+                  m->d_mlp_frag,
                   m->d_bdesc, m->d_boff, m->d_net_stalls, m->d_rg, m->d_gnu, m->d_rgf, m->d_gnuf,
                   m->d_hT, m->d_hP, m->d_hY, m->d_hTo, m->d_hYo, m->d_hit, m->d_hst};
   for (void* p : ptrs)
@@ -166,7 +166,13 @@ typedef void (*KernelFn)(Launch);
 static KernelFn select_kernel(int precision, int G, int thermo, int dft_n) {
   if (precision == STEV_MIXED) {
     const bool n13 = dft_n == 13;
-    if (thermo != STEV_THERMO_POLY) return n13 ? stev_mixed_net_kernel<13> : stev_mixed_net_kernel<0>;
+    if (thermo != STEV_THERMO_POLY) {
+      switch (G) {
+        case 8: return n13 ? stev_mixed_net_kernel<8, 13> : stev_mixed_net_kernel<8, 0>;
+        case 16: return n13 ? stev_mixed_net_kernel<16, 13> : stev_mixed_net_kernel<16, 0>;
+        default: return n13 ? stev_mixed_net_kernel<32, 13> : stev_mixed_net_kernel<32, 0>;
+      }
+    }
     switch (G) {
       case 8: return n13 ? stev_mixed_kernel<8, 13> : stev_mixed_kernel<8, 0>;
       case 16: return n13 ? stev_mixed_kernel<16, 13> : stev_mixed_kernel<16, 0>;
@@ -185,7 +191,6 @@ static KernelFn select_kernel(int precision, int G, int thermo, int dft_n) {
 // fewer lanes per cell lengthen each cell's step (the tail of the variable
 // load).  FP64: cover the species and most reactions in one or two rounds.
 static int choose_group(int S, int R, const stev_options& o) {
-  if (o.thermo != STEV_THERMO_POLY) return 32;  // the network runs one cell per warp
   if (o.lanes_per_cell) return o.lanes_per_cell;
   if (S <= 8 && R <= 32) return 8;
   if (S <= 16 && R <= 64) return 16;
@@ -208,18 +213,16 @@ static stev_status configure(stev_mechanism* m) {
   const size_t cell = mixed ? cell_smem_bytes_mixed(m->S, m->R, m->Rrev, m->opt.dft_n, net)
                             : cell_smem_bytes_fp64(m->S, m->R, m->Rrev, m->opt.dft_n);
   const size_t limit = prop.sharedMemPerBlockOptin;
-  // the network kernel adds evaluator warps and per-CTA buffers (sized here
-  // for its largest CTA)
-  const int max_cells = net ? kMaxBlockMixedNet / 32 - 2 : (mixed ? kMaxBlockMixed : kMaxBlock) / G;
-  const size_t extra = net ? net_cta_smem_bytes(max_cells) : 0;
-  if (tables + extra + cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
-  int cells = (int)((limit - tables - extra) / cell);
+  const size_t per_cell = cell;
+  const int max_cells = (mixed ? kMaxBlockMixed : kMaxBlock) / G;
+  if (tables + per_cell > limit) return fail(STEV_EINVAL, "mechanism does not fit in shared memory");
+  int cells = (int)((limit - tables) / per_cell);
   cells = std::min(cells, max_cells);
   const int per_warp = 32 / G;
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
-  const size_t smem = tables + (size_t)cells * cell + (net ? net_cta_smem_bytes(cells) : 0);
-  const int block = cells * G + (net ? 32 * net_evaluators(cells) : 0);
+  const size_t smem = tables + (size_t)cells * per_cell;
+  const int block = cells * G;
   const void* k = reinterpret_cast<const void*>(select_kernel(m->opt.precision, G, m->opt.thermo,
                                                               m->opt.dft_n));
   // a kernel compiled for this mechanism: reused if its key is unchanged; a
@@ -652,10 +655,8 @@ static Launch make_launch(stev_mechanism* m, long long n, double dt) {
   if (m->opt.thermo != STEV_THERMO_POLY && m->mlp_ready) {
     L.mlp = mlp_infer_view(m);
     L.mlp_h = m->opt.thermo == STEV_THERMO_MLP_CPH;
-    L.mlp_needed = ((L.mlp_h ? 2 : 1) * m->S + 7) / 8 * 8;
+    L.mlp_needed = (L.mlp_h ? 2 : 1) * m->S;
   }
-  L.net_cells = m->cells;
-  L.net_stalls = m->d_net_stalls;
   L.general = m->general;
   L.rg_tab = m->d_rg;
   L.g_nu = m->d_gnu;
@@ -961,6 +962,14 @@ extern "C" stev_status stev_solve_host_noalloc(stev_mechanism* m, long n, const 
 }
 
 // ------------------------------------------------------- thermo network
+// Fragment-ordered copy of the network (MlpFrag): sizes and offsets of its
+// parts in one buffer, each 16-byte aligned.
+static int mlp_frag_mt3(int n_out) { return (n_out + 15) / 16; }
+static size_t mlp_frag_bytes(int n_out) {
+  const size_t mt3 = (size_t)mlp_frag_mt3(n_out);
+  return 16 * 32 * 16 + mt3 * 4 * 32 * 16 + 4 * 32 * 8 + mt3 * 32 * 16 + kHid * 8;
+}
+
 static stev_status mlp_ensure(stev_mechanism* m) {
   if (m->d_mlp_params) return STEV_OK;
   m->mlp_out = 3 * m->S;
@@ -970,13 +979,71 @@ static stev_status mlp_ensure(stev_mechanism* m) {
   CUDA_TRY(cudaMalloc(&m->d_mlp_W2, (size_t)kHid * kHid * sizeof(__nv_bfloat16)));
   CUDA_TRY(cudaMalloc(&m->d_mlp_W3, (size_t)m->mlp_out_pad * kHid * sizeof(__nv_bfloat16)));
   CUDA_TRY(cudaMalloc(&m->d_mlp_misc, (size_t)(3 * kHid + 3 * m->mlp_out_pad) * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&m->d_mlp_frag, mlp_frag_bytes(m->mlp_out)));
   return STEV_OK;
+}
+
+
+// BF16 pair (lo in the low half) of two FP32 values, rounded to nearest even.
+static unsigned pack_bf16_host(float lo, float hi) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+  unsigned short ua, ub;
+  std::memcpy(&ua, &a, 2);
+  std::memcpy(&ub, &b, 2);
+  return (unsigned)ua | ((unsigned)ub << 16);
+}
+
+// The A fragment words of tile (mt, kt) of a row-major [rows][64] weight
+// matrix W for lane l (rows beyond n_rows are zero): see MlpFrag.
+static void frag_tile(const float* W, int n_rows, int mt, int kt, int l, unsigned out[4]) {
+  const int g = l / 4, q = l % 4;
+  auto w = [&](int r, int c) { return r < n_rows ? W[(size_t)r * kHid + c] : 0.0f; };
+  const int r0 = 16 * mt + g, r1 = r0 + 8, c0 = 16 * kt + 2 * q, c1 = c0 + 8;
+  out[0] = pack_bf16_host(w(r0, c0), w(r0, c0 + 1));
+  out[1] = pack_bf16_host(w(r1, c0), w(r1, c0 + 1));
+  out[2] = pack_bf16_host(w(r0, c1), w(r0, c1 + 1));
+  out[3] = pack_bf16_host(w(r1, c1), w(r1, c1 + 1));
 }
 
 // FP32 master parameters (host copy) + standardisation -> inference buffers
 static stev_status mlp_pack(stev_mechanism* m, const std::vector<float>& P,
                             const std::vector<float>& mean, const std::vector<float>& stdv) {
   const MlpOffsets o = mlp_offsets(m->mlp_out);
+  {
+    // fragment order: W2 tiles, W3 tiles, b2 pairs, layer-3 (scale, offset), (W1, b1)
+    const int no = m->mlp_out, mt3 = mlp_frag_mt3(no);
+    std::vector<unsigned char> buf(mlp_frag_bytes(no), 0);
+    unsigned* w2f = reinterpret_cast<unsigned*>(buf.data());
+    unsigned* w3f = w2f + 16 * 32 * 4;
+    float* b2f = reinterpret_cast<float*>(w3f + (size_t)mt3 * 4 * 32 * 4);
+    float* o3f = b2f + 4 * 32 * 2;
+    float* w1f = o3f + (size_t)mt3 * 32 * 4;
+    for (int mt = 0; mt < 4; ++mt)
+      for (int kt = 0; kt < 4; ++kt)
+        for (int l = 0; l < 32; ++l) frag_tile(&P[o.W2], kHid, mt, kt, l, w2f + ((mt * 4 + kt) * 32 + l) * 4);
+    for (int mt = 0; mt < mt3; ++mt)
+      for (int kt = 0; kt < 4; ++kt)
+        for (int l = 0; l < 32; ++l) frag_tile(&P[o.W3], no, mt, kt, l, w3f + ((mt * 4 + kt) * 32 + l) * 4);
+    for (int mt = 0; mt < 4; ++mt)
+      for (int l = 0; l < 32; ++l) {
+        b2f[(mt * 32 + l) * 2] = P[o.b2 + 16 * mt + l / 4];
+        b2f[(mt * 32 + l) * 2 + 1] = P[o.b2 + 16 * mt + l / 4 + 8];
+      }
+    for (int mt = 0; mt < mt3; ++mt)
+      for (int l = 0; l < 32; ++l)
+        for (int h = 0; h < 2; ++h) {
+          const int r = 16 * mt + l / 4 + 8 * h;
+          const float sd = r < no ? stdv[r] : 1.0f, mu = r < no ? mean[r] : 0.0f;
+          const float b3 = r < no ? P[o.b3 + r] : 0.0f;
+          o3f[(mt * 32 + l) * 4 + 2 * h] = sd;
+          o3f[(mt * 32 + l) * 4 + 2 * h + 1] = std::fmaf(b3, sd, mu);
+        }
+    for (int k = 0; k < kHid; ++k) {
+      w1f[2 * k] = P[o.W1 + k];
+      w1f[2 * k + 1] = P[o.b1 + k];
+    }
+    CUDA_TRY(cudaMemcpy(m->d_mlp_frag, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  }
   std::vector<__nv_bfloat16> w2((size_t)kHid * kHid), w3((size_t)m->mlp_out_pad * kHid);
   for (int k = 0; k < kHid * kHid; ++k) w2[k] = __float2bfloat16_rn(P[o.W2 + k]);
   for (int r = 0; r < m->mlp_out_pad; ++r)
@@ -1016,6 +1083,14 @@ static MlpInfer mlp_infer_view(const stev_mechanism* m) {
   w.stdv = w.mean + m->mlp_out_pad;
   w.n_out = m->mlp_out_pad;
   w.n_valid = m->mlp_out;
+  const int mt3 = mlp_frag_mt3(m->mlp_out);
+  const unsigned char* base = m->d_mlp_frag;
+  w.frag.W2 = reinterpret_cast<const uint4*>(base);
+  w.frag.W3 = w.frag.W2 + 16 * 32;
+  w.frag.b2 = reinterpret_cast<const float2*>(w.frag.W3 + (size_t)mt3 * 4 * 32);
+  w.frag.o3 = reinterpret_cast<const float4*>(w.frag.b2 + 4 * 32);
+  w.frag.w1 = reinterpret_cast<const float2*>(w.frag.o3 + (size_t)mt3 * 32);
+  w.frag.mt3 = mt3;
   return w;
 }
 
@@ -1186,11 +1261,12 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   if (st != STEV_OK) return st;
   const int no = m->mlp_out, np = m->mlp_np;
   const int mb_tiles = (int)((std::min((long long)batch, (long long)n) + kMlpTile - 1) / kMlpTile);
-  double *dT = nullptr, *dloss = nullptr, *dlp = nullptr;
+  double *dT = nullptr, *dlp = nullptr, *dlep = nullptr;
   float *dtarget = nullptr, *dpart = nullptr, *dm1 = nullptr, *dm2 = nullptr;
+  float4* dsched = nullptr;
   auto cleanup = [&]() {
-    cudaFree(dT); cudaFree(dloss); cudaFree(dtarget); cudaFree(dpart);
-    cudaFree(dm1); cudaFree(dm2); cudaFree(dlp);
+    cudaFree(dT); cudaFree(dtarget); cudaFree(dpart); cudaFree(dm1); cudaFree(dm2);
+    cudaFree(dlp); cudaFree(dlep); cudaFree(dsched);
   };
 #define TRY_CLEAN(expr)                                                                     \
   do {                                                                                      \
@@ -1207,7 +1283,6 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   TRY_CLEAN(cudaMalloc(&dlp, (size_t)mb_tiles * 8));
   TRY_CLEAN(cudaMalloc(&dm1, (size_t)np * 4));
   TRY_CLEAN(cudaMalloc(&dm2, (size_t)np * 4));
-  TRY_CLEAN(cudaMalloc(&dloss, 8));
   TRY_CLEAN(cudaMemcpy(dT, T_samples, (size_t)n * 8, cudaMemcpyHostToDevice));
   // targets: the polynomials in FP64, standardised per output column
   std::vector<float> mean, stdv;
@@ -1225,31 +1300,46 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
   TRY_CLEAN(cudaMemset(dm1, 0, (size_t)np * 4));
   TRY_CLEAN(cudaMemset(dm2, 0, (size_t)np * 4));
   // Adam over minibatches in sample order (the samples are drawn
-  // independently), the step size decaying from lr to lr/100 along a cosine
+  // independently), the step size decaying from lr to lr/100 along a cosine;
+  // every step in one cooperative launch (mlp_train_kernel), the schedule
+  // computed here
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const long long per_epoch = (n + batch - 1) / batch, total = per_epoch * epochs;
-  long long step = 0;
-  for (int ep = 0; ep < epochs; ++ep) {
-    TRY_CLEAN(cudaMemset(dloss, 0, 8));
-    for (long long s0 = 0; s0 < n; s0 += batch) {
-      const long long nb = std::min((long long)batch, (long long)n - s0);
-      const int tiles = (int)((nb + kMlpTile - 1) / kMlpTile);
-      st = mlp_grad_device(m, m->d_mlp_params, dT + s0, dtarget + s0 * no, nb, nb, dpart, dlp, 0);
-      if (st != STEV_OK) { cleanup(); return st; }
-      const double frac = (double)step / (double)std::max(total - 1, 1LL);
-      const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac))));
-      ++step;
-      // each minibatch's squared errors are relative to its own mean; averaged below
-      const float bc1 = 1.0f - std::pow(b1, (float)step), bc2 = 1.0f - std::pow(b2, (float)step);
-      mlp_adam_kernel<<<(np + 255) / 256, 256>>>(m->d_mlp_params, dpart, tiles, dlp, dloss, dm1,
-                                                 dm2, np, lr_t, b1, b2, eps, bc1, bc2);
-      TRY_CLEAN(cudaGetLastError());
-    }
-    if (loss_per_epoch) {
-      double l = 0.0;
-      TRY_CLEAN(cudaMemcpy(&l, dloss, 8, cudaMemcpyDeviceToHost));
-      loss_per_epoch[ep] = (float)(l / ((double)n * no));
-    }
+  std::vector<float4> sched((size_t)total);
+  for (long long step = 0; step < total; ++step) {
+    const double frac = (double)step / (double)std::max(total - 1, 1LL);
+    const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+    const float t = (float)(step + 1);
+    sched[(size_t)step] = make_float4(lr_t, 1.0f - std::pow(b1, t), 1.0f - std::pow(b2, t), 0.0f);
+  }
+  TRY_CLEAN(cudaMalloc(&dsched, sched.size() * sizeof(float4)));
+  TRY_CLEAN(cudaMalloc(&dlep, (size_t)epochs * 8));
+  TRY_CLEAN(cudaMemcpy(dsched, sched.data(), sched.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  TRY_CLEAN(cudaMemset(dlep, 0, (size_t)epochs * 8));
+  {
+    const size_t smem = mlp_grad_smem_bytes(no);
+    TRY_CLEAN(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    TRY_CLEAN(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_train_kernel, kMlpTile, smem));
+    TRY_CLEAN(cudaGetDevice(&dev));
+    TRY_CLEAN(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) { cleanup(); return fail(STEV_EINVAL, "training kernel cannot be resident"); }
+    const int grid = std::min(mb_tiles, per_sm * sms);
+    int no_ = no;
+    long long n_ = n, total_ = total, per_epoch_ = per_epoch;
+    int batch_ = batch;
+    float* pp = m->d_mlp_params;
+    float b1_ = b1, b2_ = b2, eps_ = eps;
+    void* args[] = {&pp, &no_, &dT, &dtarget, &n_, &batch_, &dsched, &total_, &per_epoch_, &dpart,
+                    &dlp, &dm1, &dm2, &dlep, &b1_, &b2_, &eps_};
+    TRY_CLEAN(cudaLaunchCooperativeKernel((const void*)mlp_train_kernel, dim3(grid), dim3(kMlpTile),
+                                          args, smem, 0));
+    TRY_CLEAN(cudaGetLastError());
+  }
+  if (loss_per_epoch) {
+    std::vector<double> l(epochs);
+    TRY_CLEAN(cudaMemcpy(l.data(), dlep, (size_t)epochs * 8, cudaMemcpyDeviceToHost));
+    for (int ep = 0; ep < epochs; ++ep) loss_per_epoch[ep] = (float)(l[ep] / ((double)n * no));
   }
   TRY_CLEAN(cudaMemcpy(P.data(), m->d_mlp_params, (size_t)np * 4, cudaMemcpyDeviceToHost));
 #undef TRY_CLEAN
@@ -1258,15 +1348,26 @@ extern "C" stev_status stev_mlp_train(stev_mechanism* m, const double* T_samples
 }
 
 // --------------------------------------- Levenberg-Marquardt training
+static stev_status launch_jacobian_t(int no, const float* dp, const double* dT, const float* dtg,
+                                     long long nsamp, float* dJt, long long ldk, float* dr) {
+  const size_t smem = mlp_jacobian_smem_bytes(no);
+  CUDA_TRY(cudaFuncSetAttribute(mlp_jacobian_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  mlp_jacobian_t_kernel<<<(unsigned)nsamp, kJacThreads, smem>>>(dp, no, dT, dtg, dJt, ldk, dr);
+  CUDA_TRY(cudaGetLastError());
+  return STEV_OK;
+}
+
 extern "C" stev_status stev_mlp_jacobian(stev_mechanism* m, const float* params, const double* T,
                                          long n, float* J) {
   g_err.clear();
   if (!m || !params || !T || !J) return fail(STEV_EINVAL, "NULL argument");
   if (n < 1 || n > 4096) return fail(STEV_EINVAL, "n must be in [1, 4096]");
   const int no = 3 * m->S, np = mlp_n_params(no);
-  float *dp = nullptr, *dJ = nullptr, *dtg = nullptr, *dr = nullptr;
+  const long long rows = (long long)n * no, ldk = (rows + 3) / 4 * 4;
+  float *dp = nullptr, *dJt = nullptr, *dtg = nullptr, *dr = nullptr;
   double* dT = nullptr;
-  auto cleanup = [&]() { cudaFree(dp); cudaFree(dJ); cudaFree(dtg); cudaFree(dr); cudaFree(dT); };
+  auto cleanup = [&]() { cudaFree(dp); cudaFree(dJt); cudaFree(dtg); cudaFree(dr); cudaFree(dT); };
 #define TRY_CLEAN(expr)                                                                     \
   do {                                                                                      \
     cudaError_t e_ = (expr);                                                                \
@@ -1277,16 +1378,21 @@ extern "C" stev_status stev_mlp_jacobian(stev_mechanism* m, const float* params,
     }                                                                                       \
   } while (0)
   TRY_CLEAN(cudaMalloc(&dp, (size_t)np * 4));
-  TRY_CLEAN(cudaMalloc(&dJ, (size_t)n * no * np * 4));
-  TRY_CLEAN(cudaMalloc(&dtg, (size_t)n * no * 4));
-  TRY_CLEAN(cudaMalloc(&dr, (size_t)n * no * 4));
+  TRY_CLEAN(cudaMalloc(&dJt, (size_t)np * ldk * 4));
+  TRY_CLEAN(cudaMalloc(&dtg, (size_t)rows * 4));
+  TRY_CLEAN(cudaMalloc(&dr, (size_t)rows * 4));
   TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
   TRY_CLEAN(cudaMemcpy(dp, params, (size_t)np * 4, cudaMemcpyHostToDevice));
   TRY_CLEAN(cudaMemcpy(dT, T, (size_t)n * 8, cudaMemcpyHostToDevice));
-  TRY_CLEAN(cudaMemset(dtg, 0, (size_t)n * no * 4));
-  mlp_jacobian_kernel<<<(unsigned)n, kHid>>>(dp, no, dT, dtg, dJ, dr);
-  TRY_CLEAN(cudaGetLastError());
-  TRY_CLEAN(cudaMemcpy(J, dJ, (size_t)n * no * np * 4, cudaMemcpyDeviceToHost));
+  TRY_CLEAN(cudaMemset(dtg, 0, (size_t)rows * 4));
+  {
+    const stev_status st = launch_jacobian_t(no, dp, dT, dtg, n, dJt, ldk, dr);
+    if (st != STEV_OK) { cleanup(); return st; }
+  }
+  std::vector<float> jt((size_t)np * ldk);
+  TRY_CLEAN(cudaMemcpy(jt.data(), dJt, jt.size() * 4, cudaMemcpyDeviceToHost));
+  for (long long r = 0; r < rows; ++r)
+    for (int q = 0; q < np; ++q) J[(size_t)r * np + q] = jt[(size_t)q * ldk + r];
 #undef TRY_CLEAN
   cleanup();
   return STEV_OK;
@@ -1307,20 +1413,17 @@ extern "C" stev_status stev_mlp_train_lm(stev_mechanism* m, const double* T_samp
   if (st != STEV_OK) return st;
   const int no = m->mlp_out, np = m->mlp_np;
   const long long nb = std::min((long long)batch, (long long)n);
-  const long long rows = nb * no;
-  if ((double)rows * np * 4 > 8e9) return fail(STEV_EINVAL, "batch too large (Jacobian over 8 GB)");
-  double *dT = nullptr, *dAd = nullptr, *dg = nullptr, *dse = nullptr, *dwork = nullptr;
-  float *dtarget = nullptr, *dJ = nullptr, *dr = nullptr, *dA = nullptr, *dgf = nullptr;
-  float *dp = nullptr, *dpn = nullptr;
-  int* dinfo = nullptr;
-  cublasHandle_t cb = nullptr;
-  cusolverDnHandle_t cs = nullptr;
+  const long long rows = nb * no, ldk = (rows + 3) / 4 * 4, lda = ((long long)np + 3) / 4 * 4;
+  if ((double)np * ldk * 4 > 8e9) return fail(STEV_EINVAL, "batch too large (Jacobian over 8 GB)");
+  double *dT = nullptr, *dse = nullptr;
+  float *dtarget = nullptr, *dJt = nullptr, *dr = nullptr, *dA = nullptr, *dg = nullptr;
+  float *dd = nullptr, *dp = nullptr, *dpn = nullptr;
+  int* derr = nullptr;
+  stev::host::CgWork cgw{};
   auto cleanup = [&]() {
-    cudaFree(dT); cudaFree(dAd); cudaFree(dg); cudaFree(dse); cudaFree(dwork); cudaFree(dtarget);
-    cudaFree(dJ); cudaFree(dr); cudaFree(dA); cudaFree(dgf); cudaFree(dp); cudaFree(dpn);
-    cudaFree(dinfo);
-    if (cb) cublasDestroy(cb);
-    if (cs) cusolverDnDestroy(cs);
+    cudaFree(dT); cudaFree(dse); cudaFree(dtarget); cudaFree(dJt); cudaFree(dr); cudaFree(dA);
+    cudaFree(dg); cudaFree(dd); cudaFree(dp); cudaFree(dpn); cudaFree(derr);
+    stev::host::cg_work_free(&cgw);
   };
 #define TRY_CLEAN(expr)                                                                     \
   do {                                                                                      \
@@ -1331,32 +1434,28 @@ extern "C" stev_status stev_mlp_train_lm(stev_mechanism* m, const double* T_samp
                   #expr, cudaGetErrorString(e_));                                           \
     }                                                                                       \
   } while (0)
-#define LIB_CLEAN(expr, what)                                                               \
-  do {                                                                                      \
-    if ((expr) != 0) {                                                                      \
-      cleanup();                                                                            \
-      return fail(STEV_ECUDA, "%s failed", what);                                           \
-    }                                                                                       \
+#define ST_CLEAN(expr)                 \
+  do {                                 \
+    const stev_status s_ = (expr);     \
+    if (s_ != STEV_OK) {               \
+      cleanup();                       \
+      return s_;                       \
+    }                                  \
   } while (0)
   TRY_CLEAN(cudaMalloc(&dT, (size_t)n * 8));
   TRY_CLEAN(cudaMalloc(&dtarget, (size_t)n * no * 4));
-  TRY_CLEAN(cudaMalloc(&dJ, (size_t)rows * np * 4));
-  TRY_CLEAN(cudaMalloc(&dr, (size_t)rows * 4));
-  TRY_CLEAN(cudaMalloc(&dA, (size_t)np * np * 4));
-  TRY_CLEAN(cudaMalloc(&dAd, (size_t)np * np * 8));
-  TRY_CLEAN(cudaMalloc(&dgf, (size_t)np * 4));
-  TRY_CLEAN(cudaMalloc(&dg, (size_t)np * 8));
+  TRY_CLEAN(cudaMalloc(&dJt, (size_t)np * ldk * 4));
+  TRY_CLEAN(cudaMalloc(&dr, (size_t)ldk * 4));
+  TRY_CLEAN(cudaMalloc(&dA, (size_t)np * lda * 4));
+  TRY_CLEAN(cudaMalloc(&dg, (size_t)np * 4));
+  TRY_CLEAN(cudaMalloc(&dd, (size_t)np * 4));
   TRY_CLEAN(cudaMalloc(&dse, (size_t)nb * 8));
   TRY_CLEAN(cudaMalloc(&dp, (size_t)np * 4));
   TRY_CLEAN(cudaMalloc(&dpn, (size_t)np * 4));
-  TRY_CLEAN(cudaMalloc(&dinfo, sizeof(int)));
-  LIB_CLEAN(cublasCreate(&cb), "cublasCreate");
-  LIB_CLEAN(cublasSetMathMode(cb, CUBLAS_PEDANTIC_MATH), "cublasSetMathMode");  // FP32, no TF32
-  LIB_CLEAN(cusolverDnCreate(&cs), "cusolverDnCreate");
-  int lwork = 0;
-  LIB_CLEAN(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, np, dAd, np, &lwork),
-            "cusolverDnDpotrf_bufferSize");
-  TRY_CLEAN(cudaMalloc(&dwork, (size_t)std::max(lwork, 1) * 8));
+  TRY_CLEAN(cudaMalloc(&derr, sizeof(int)));
+  TRY_CLEAN(cudaMemset(derr, 0, sizeof(int)));
+  TRY_CLEAN(cudaMemset(dr, 0, (size_t)ldk * 4));
+  ST_CLEAN(stev::host::cg_work_alloc(&cgw, np));
   TRY_CLEAN(cudaMemcpy(dT, T_samples, (size_t)n * 8, cudaMemcpyHostToDevice));
 
   // targets (statistics kept when continuing) and starting parameters
@@ -1364,11 +1463,9 @@ extern "C" stev_status stev_mlp_train_lm(stev_mechanism* m, const double* T_samp
   if (init == 1) {
     mean.resize(no);
     stdv.resize(no);
-    st = stev_mlp_get_params(m, P.data(), np, mean.data(), stdv.data());
-    if (st != STEV_OK) { cleanup(); return st; }
+    ST_CLEAN(stev_mlp_get_params(m, P.data(), np, mean.data(), stdv.data()));
   }
-  st = mlp_make_targets(m, dT, n, dtarget, mean, stdv, init == 0);
-  if (st != STEV_OK) { cleanup(); return st; }
+  ST_CLEAN(mlp_make_targets(m, dT, n, dtarget, mean, stdv, init == 0));
   if (init == 0) {
     const MlpOffsets o = mlp_offsets(no);
     uint64_t rs = seed;
@@ -1389,41 +1486,30 @@ extern "C" stev_status stev_mlp_train_lm(stev_mechanism* m, const double* T_samp
     *out = t / (double)rows;
     return true;
   };
+  // Per iteration: the batch's transposed Jacobian, the Gauss-Newton matrix
+  // A = J^T J (TF32 tensor cores, FP32 accumulation) and g = J^T r; then
+  // Marquardt's damped system (A + lambda diag A) d = g by preconditioned
+  // conjugate gradients (relative residual 1e-3, at most kLmCgIters steps: an
+  // inexact Levenberg-Marquardt step), accepted if the batch loss falls.
+  const int kLmCgIters = 400;
+  const double kLmCgTol = 1e-3, kLmEps = 1e-12;
   double lambda = lambda0;
-  const float one = 1.0f, zero = 0.0f;
   for (int it = 0; it < iterations; ++it) {
     const long long s0 = ((long long)it * nb) % std::max(1LL, (long long)n - nb + 1);
-    mlp_jacobian_kernel<<<(unsigned)nb, kHid>>>(dp, no, dT + s0, dtarget + s0 * no, dJ, dr);
-    TRY_CLEAN(cudaGetLastError());
-    // J is row-major [rows][np], i.e. column-major np x rows: A = J^T J, g = J^T r
-    LIB_CLEAN(cublasSsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, np, (int)rows, &one, dJ, np,
-                          &zero, dA, np), "cublasSsyrk");
-    LIB_CLEAN(cublasSgemv(cb, CUBLAS_OP_N, np, (int)rows, &one, dJ, np, dr, 1, &zero, dgf, 1),
-              "cublasSgemv");
+    ST_CLEAN(launch_jacobian_t(no, dp, dT + s0, dtarget + s0 * no, nb, dJt, ldk, dr));
+    ST_CLEAN(stev::host::gram_tf32(dJt, np, rows, ldk, dA, lda, derr, 0));
+    ST_CLEAN(stev::host::rows_dot(dJt, np, rows, ldk, dr, dg, 0));
     double loss0 = 0.0, loss1 = 0.0;
     if (!batch_loss(dp, s0, &loss0)) { cleanup(); return fail(STEV_ECUDA, "loss copy failed"); }
+    int herr = 0;
+    TRY_CLEAN(cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) { cleanup(); return fail(STEV_ETIMEOUT, "Gauss-Newton matrix: a pipeline wait timed out"); }
     bool accepted = false;
     for (int attempt = 0; attempt < 8 && !accepted; ++attempt) {
-      const long long tot = (long long)np * np;
-      mlp_damp_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(dA, np, lambda, 1e-12, dAd);
-      TRY_CLEAN(cudaGetLastError());
-      LIB_CLEAN(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, np, dAd, np, dwork, lwork, dinfo),
-                "cusolverDnDpotrf");
-      int info = 0;
-      TRY_CLEAN(cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
-      if (info != 0) {  // not positive definite at this damping
-        lambda *= 4.0;
-        continue;
-      }
-      // g (FP64) = J^T r; solve (A + lambda diag A) d = g; p_new = p - d
-      std::vector<float> gf(np);
-      std::vector<double> gd(np);
-      TRY_CLEAN(cudaMemcpy(gf.data(), dgf, (size_t)np * 4, cudaMemcpyDeviceToHost));
-      for (int k = 0; k < np; ++k) gd[k] = gf[k];
-      TRY_CLEAN(cudaMemcpy(dg, gd.data(), (size_t)np * 8, cudaMemcpyHostToDevice));
-      LIB_CLEAN(cusolverDnDpotrs(cs, CUBLAS_FILL_MODE_LOWER, np, 1, dAd, np, dg, np, dinfo),
-                "cusolverDnDpotrs");
-      mlp_step_kernel<<<(np + 255) / 256, 256>>>(dp, dg, np, dpn);
+      int cg_it = 0;
+      ST_CLEAN(stev::host::damped_cg(dA, np, lda, dg, lambda, kLmEps, dd, kLmCgIters, kLmCgTol, &cg_it,
+                                     &cgw, 0));
+      mlp_step_kernel<<<(np + 255) / 256, 256>>>(dp, dd, np, dpn);
       TRY_CLEAN(cudaGetLastError());
       if (!batch_loss(dpn, s0, &loss1)) { cleanup(); return fail(STEV_ECUDA, "loss copy failed"); }
       if (std::isfinite(loss1) && loss1 < loss0) {
@@ -1438,7 +1524,7 @@ extern "C" stev_status stev_mlp_train_lm(stev_mechanism* m, const double* T_samp
   }
   TRY_CLEAN(cudaMemcpy(P.data(), dp, (size_t)np * 4, cudaMemcpyDeviceToHost));
 #undef TRY_CLEAN
-#undef LIB_CLEAN
+#undef ST_CLEAN
   cleanup();
   return mlp_pack(m, P, mean, stdv);
 }

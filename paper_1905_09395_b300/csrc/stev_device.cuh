@@ -38,7 +38,6 @@ constexpr double kPatm = 101325.0;      // Pa, standard state of Eq. 30
 constexpr int kNone = 0xFF;
 constexpr int kMaxBlock = 512;       // threads per CTA of the FP64 persistent kernel
 constexpr int kMaxBlockMixed = 768;  // threads per CTA of the mixed persistent kernel
-constexpr int kMaxBlockMixedNet = 768;  // ... with the thermo network: cell warps + 2 evaluators
 
 enum { SP_W = 0, SP_INVW = 1, SP_TSPLIT = 2, SP_LOW = 4, SP_HIGH = 18, SP_STRIDE = 32 };
 enum { B_A0 = 0, B_A1, B_A2, B_A3, B_A4, B_A5, B_A6, B_H1, B_H2, B_H3, B_H4, B_G2, B_G3, B_G4,
@@ -62,9 +61,27 @@ __host__ __device__ inline int gather_pack(int r, int nu) { return r * 16 + (nu 
 __constant__ double kNuOf[16] = {0, 0, 0, 0, 0, 0, -2.0, -1.0, 0, 1.0, 2.0, 0, 0, 0, 0, 0};
 __constant__ float kNuOfF[16] = {0, 0, 0, 0, 0, 0, -2.0f, -1.0f, 0, 1.0f, 2.0f, 0, 0, 0, 0, 0};
 
+// The network's weights in MMA fragment order for inference inside the solver
+// (the weights are the A operand of m16n8k16, 16 output units per tile; the
+// cells are the columns of B): for tile (mt, kt) lane l holds the four 32-bit
+// words a0..a3 of the A layout of the PTX ISA, BF16 pairs of
+//   a0: W[16 mt + g][16 kt + 2 q + {0, 1}]      a1: the same for row g + 8
+//   a2: W[16 mt + g][16 kt + 8 + 2 q + {0, 1}]  a3: the same for row g + 8
+// with g = l / 4, q = l % 4, so that one 16-byte load per lane fetches a tile.
+struct MlpFrag {
+  const uint4* W2;   // [4 mt][4 kt][32 lanes]
+  const uint4* W3;   // [mt3][4 kt][32 lanes], rows = outputs (cp/R, H/R, S/R of each species)
+  const float2* b2;  // [4 mt][32 lanes]: b2 of rows 16 mt + g and 16 mt + g + 8
+  const float4* o3;  // [mt3][32 lanes]: (scale, offset) of the same two rows of layer 3,
+                     //   value = (W3 a2) * scale + offset, scale = std, offset = b3 std + mean
+  const float2* w1;  // [64]: (W1, b1) of each hidden unit of layer 1
+  int mt3;           // m-tiles of W3 packed: 3S output rows rounded up to 16
+};
+
 // Inference weights: W2 and W3 rows in BF16 (row-major [out][in]: a row of W
 // is a column of the MMA's B operand, so B fragments are direct 32-bit loads),
-// W1, b1, b2, b3, mean, std in FP32.
+// W1, b1, b2, b3, mean, std in FP32 (the batched evaluation kernel); and the
+// same network in fragment order (the solver kernels).
 struct MlpInfer {
   const __nv_bfloat16* W2;  // [64][64]
   const __nv_bfloat16* W3;  // [n_out][64]
@@ -76,6 +93,7 @@ struct MlpInfer {
   const float* stdv;        // [n_out]
   int n_out;                // padded to a multiple of 8
   int n_valid;              // 3S: columns written to the caller's array
+  MlpFrag frag;
 };
 
 
@@ -138,10 +156,8 @@ struct Launch {
   // the options in FP32 for the mixed kernels (converted once, not per use)
   float y_step_max_f, alpha_f, tol_ring_f, tol_freq_f, r_fac_f, inv_r_fac_f, rof_min_f;
   MlpInfer mlp;           // thermo network (mixed kernel, thermo = MLP)
-  int mlp_needed;         // network outputs the solver reads (cp/R [, H/R]), rounded up to 8
+  int mlp_needed;         // network output rows the solver reads: S (cp/R) or 2S (and H/R)
   int mlp_h;              // 1: H/RT from the network as well
-  int net_cells;          // network kernel: cell warps per CTA (one more warp evaluates)
-  unsigned long long* net_stalls;  // cell-steps whose network answer timed out (polynomials used)
 };
 
 constexpr double kMlpTLow = 300.0, kMlpTHigh = 3000.0;  // network's training range (K)
@@ -175,27 +191,20 @@ __host__ __device__ inline size_t table_smem_bytes_mixed(int S, int R, int n_gat
 
 // Mixed kernel cell: the Gibbs terms g2 as float pairs (S + 1: the last is
 // the unused-slot entry), Y as float pairs in two arrays (hi, lo), C (S + 1)
-// and H/RT (S), rates (R), history [Rrev][N | 1] and rOF (Rrev) in FP32; with
-// the thermo network also the cell's row of network outputs (2S rounded up
-// to 8).
+// and H/RT (S), rates (R), history [Rrev][N | 1] and rOF (Rrev) in FP32.
+// With the thermo network the rate array also holds, at the start of each
+// step before the rates are computed, the cell's network activations and
+// outputs (mixed_q_len).
+__host__ __device__ inline int mixed_q_len(int S, int R, bool mlp) {
+  // network scratch: layer-1 and layer-2 activations (64 BF16 each = 64
+  // floats' room), then the outputs cp/R and H/R (2S, whole 16-row tiles)
+  const int net = 64 + (2 * S + 15) / 16 * 16;
+  return mlp ? (R > net ? R : net) : R;
+}
 __host__ __device__ inline size_t cell_smem_bytes_mixed(int S, int R, int Rrev, int dft_n,
                                                        bool mlp = false) {
   size_t b = (size_t)8 * (S + 1) +
-             ((size_t)4 * S + 1 + R + (size_t)(dft_n | 1) * Rrev + Rrev) * 4;
-  if (mlp) b += (size_t)((2 * S + 7) / 8 * 8) * 4;
+             ((size_t)4 * S + 1 + mixed_q_len(S, R, mlp) + (size_t)(dft_n | 1) * Rrev + Rrev) * 4;
   return (b + 15) & ~(size_t)15;
-}
-
-// The network kernel's evaluator warps: two (each answering half of the
-// CTA's cells, at most 16 rows) unless the CTA holds 8 cells or fewer.
-__host__ __device__ inline int net_evaluators(int cells) { return cells > 8 ? 2 : 1; }
-
-// Per-CTA buffers of the network kernel for `cells` resident cells (one per
-// warp, at most 32): the published scaled temperatures and request / answer /
-// waiting tags, each evaluator's 16 temperatures and 16 x 72 BF16 activation tile, and
-// the count of cell warps still running.
-constexpr int kNetActLd = 64 + 8;
-__host__ __device__ inline size_t net_cta_smem_bytes(int cells) {
-  return (size_t)32 * 4 * 4 + (size_t)net_evaluators(cells) * (16 * 4 + 16 * kNetActLd * 2) + 16;
 }
 }  // namespace stev

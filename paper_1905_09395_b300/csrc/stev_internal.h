@@ -55,5 +55,30 @@ stev_status spec_compile(const SpecKey& k, std::vector<char>* cubin, std::string
 // Compiles and loads it into the current device's primary context.
 stev_status spec_load(const SpecKey& k, cudaLibrary_t* lib, cudaKernel_t* kernel);
 
+// Linear algebra of the Levenberg-Marquardt trainer (stev_lm.cu), device
+// pointers, asynchronous on s unless stated.
+// G = X X^T (n x n, full) for X [n][ldx] row-major (k columns used; ldx a
+// multiple of 4, X 16-byte aligned), TF32 tensor-core products accumulated in
+// FP32; *d_err (device) is set if a pipeline wait timed out.
+stev_status gram_tf32(const float* X, long long n, long long k, long long ldx, float* G,
+                      long long ldg, int* d_err, cudaStream_t s);
+// g = X r (X as above, r 16-byte aligned).
+stev_status rows_dot(const float* X, long long n, long long k, long long ldx, const float* r,
+                     float* g, cudaStream_t s);
+// Work arrays of damped_cg for systems of n unknowns.
+struct CgWork {
+  float *r, *z, *p, *q;
+  double *part, *dd;
+};
+stev_status cg_work_alloc(CgWork* w, long long n);
+void cg_work_free(CgWork* w);
+// (A + lambda diag(A) + eps I) x = b by conjugate gradients with the Jacobi
+// preconditioner, A symmetric [n][lda]; stops when the residual has fallen by
+// rtol or after max_iters; *iters gets the iterations taken.  Synchronises s
+// once per iteration (the step lengths are computed on the host).
+stev_status damped_cg(const float* A, long long n, long long lda, const float* b, double lambda,
+                      double eps, float* x, int max_iters, double rtol, int* iters, CgWork* w,
+                      cudaStream_t s);
+
 }  // namespace host
 }  // namespace stev

@@ -185,63 +185,12 @@ __device__ __forceinline__ float lg2f_approx(float x) {
   return r;
 }
 
-// The thermo network's outputs for a cell (MLP kernels): waits until the
-// evaluator has answered request net_tag (bounded; on a timeout the step
-// takes the polynomials and counts a stall), then adds Y cp/R / W to cpp
-// (and sets H/RT with L.mlp_h).  Returns the group's sum of cpp.
-template <int G>
-__device__ __forceinline__ float net_thermo(const Launch& L, const TablesF& tb, const float* cYh,
-                                            float* cH, const float* cTh,
-                                            volatile int* net_ans, int net_tag,
-                                            bool use_net, FF T, float invTf, int l, float cpp) {
-  const int S = mS(L);
-  const float Tf = T.h;
-  if (use_net) {
-    // the warp polls the answer tag together (bounded), so that the loop and
-    // its exit are warp-uniform
-    bool answered = __all_sync(0xffffffffu, *net_ans == net_tag);
-    if (!answered) {
-      if (l == 0) net_ans[32] = net_tag;  // waiting: the evaluator answers at once (row + 32 = wait tags)
-      for (int k = 0; !answered && k < (1 << 18); ++k) {
-        __nanosleep(64);
-        answered = __all_sync(0xffffffffu, *net_ans == net_tag);
-      }
-    }
-    __threadfence_block();
-    if (answered) {
-      for (int i = l; i < S; i += G) {
-        cpp = fmaf(cYh[i] * cTh[i], tb.spf[SF_INVW * S + i], cpp);
-        if (L.mlp_h) cH[i] = cTh[S + i] * invTf;  // the network gives H/R
-      }
-    } else {
-      if (l == 0) atomicAdd(L.net_stalls, 1ULL);
-      for (int i = l; i < S; i += G) {
-        const float* f = tb.spf + i;
-        const bool lo = ff_below(T, f[SF_SPLIT_H * S], f[SF_SPLIT_L * S]);
-        const float* b = f + (lo ? SF_LOW : SF_HIGH) * S;
-        const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4 * S], Tf, b[BF_A3 * S]), Tf, b[BF_A2 * S]),
-                                    Tf, b[BF_A1 * S]), Tf, b[BF_A0 * S]);
-        cpp = fmaf(cYh[i] * cpR, f[SF_INVW * S], cpp);
-        if (L.mlp_h) {
-          const float hp = fmaf(fmaf(fmaf(b[BF_H4 * S], Tf, b[BF_H3 * S]), Tf, b[BF_H2 * S]), Tf,
-                                b[BF_H1 * S]);
-          cH[i] = fmaf(hp, Tf, b[BF_A0 * S]) + b[BF_A5 * S] * invTf;
-        }
-      }
-    }
-  }
-  return group_sum<G>(cpp);
-}
-
 // MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
 // (Sec. 3) whenever T is inside its training range; outside it, and for G/RT
-// always, the NASA-7 polynomials are used.  The CTA's evaluator warp runs the
-// network for the published temperatures of 16 cells at a time
-// (stev_mixed_net_kernel); this cell's request carries tag net_tag, and its
-// outputs (cp/R, then H/R) are in cTh once *net_ans == net_tag.  The step
-// waits for that only where it first needs them: with H/RT from the network,
-// before the production rates; with cp/R only, before the temperature update,
-// after the damper (net_thermo).
+// always, the NASA-7 polynomials are used.  The warp evaluates the network of
+// all its cells at the start of the step (net_eval_cells: BF16 tensor-core
+// MMAs with FP32 accumulation) into each cell's output row cOut, from which
+// the thermo loop reads cp/R and H/R; net_buf holds the warp's activations.
 //
 // NT > 0: the DFT window N (Eq. 9) fixed at compile time (the taps unrolled);
 // NT = 0: N = L.dft_n.  The history is reaction-major, N taps of a reaction
@@ -253,15 +202,19 @@ template <int G, bool MLP, int NT>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, float* cYh,
                                           float* cYl, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
-                                          CellState& st, const float* cTh,
-                                          volatile int* net_ans, int net_tag) {
+                                          CellState& st, float* netQ0, int cell_ld) {
   const int S = mS(L), R = mR(L), Rrev = mRrev(L);
   const int N = NT > 0 ? NT : L.dft_n;
   const int NP = N | 1;
   const FF T{st.Th, st.Tl};
   const FF lnT{st.lnTh, st.lnTl};
   const float Tf = T.h;
-  const bool use_net = MLP && in_net_range(Tf);  // one cell per warp
+  const bool use_net = MLP && in_net_range(Tf);
+  // the network's outputs for this cell, in its rate array until the rates
+  // are computed
+  const float* cOut = cQ + kNetOutOff;
+  if (MLP && __any_sync(0xffffffffu, use_net))
+    net_eval_cells<G>(L.mlp.frag, (Tf - kTMid) * (1.0f / kTHalf), netQ0, cell_ld, L.mlp_needed);
   // 1/T: the FP32 reciprocal r, then 1/T = r / (1 - e), e = 1 - T r exact to
   // ~2^-46 by FMA: lo = r (e + e^2)
   const float r0 = rcp_approx(Tf);
@@ -295,11 +248,15 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
       const float cpR = fmaf(fmaf(fmaf(fmaf(b[BF_A4 * S], Tf, b[BF_A3 * S]), Tf, b[BF_A2 * S]),
                                   Tf, b[BF_A1 * S]), Tf, b[BF_A0 * S]);
       cpp = fmaf(Yi * cpR, f[SF_INVW * S], cpp);
+    } else {
+      cpp = fmaf(Yi * cOut[i], f[SF_INVW * S], cpp);  // cp/R from the network
     }
     if (!(use_net && L.mlp_h)) {
       const float hp = fmaf(fmaf(fmaf(b[BF_H4 * S], Tf, b[BF_H3 * S]), Tf, b[BF_H2 * S]), Tf,
                             b[BF_H1 * S]);
       cH[i] = fmaf(hp, Tf, b[BF_A0 * S]) + b[BF_A5 * S] * invTf;
+    } else {
+      cH[i] = cOut[S + i] * invTf;  // the network gives H/R
     }
     float gs = g[0], ge = g[S];
     dot2_term(g[2 * S], g[3 * S], lnT, gs, ge);
@@ -314,15 +271,14 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     const float ys = (L.alpha_f > 0.0f) ? y * __fdividef(y, L.alpha_f + y) : y;
     cC[i] = rho * ys * f[SF_INVW * S];
   }
-  float cpsum = 0.0f;
-  if (!MLP) cpsum = group_sum<G>(cpp);
+  const float cpsum = group_sum<G>(cpp);
   __syncwarp();
 
   // rates of progress: kf = 2^(lg2 A + beta lg2 T - Ea/R log2e / T) (FP32);
   // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e = sum nu g2, summed
   // exactly
   const int ktap = st.nhist % N;
-#pragma unroll(MLP ? 1 : 2)  // two reactions per trip where it pays (measured)
+#pragma unroll 2  // two reactions per trip (measured)
   for (int r = l; r < R; r += G) {
     const float4 rx = tb.rxf[r];
     const int4 ri = tb.ri[r];
@@ -378,9 +334,6 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
   }
   __syncwarp();
 
-  if (MLP && L.mlp_h) cpsum = net_thermo<G>(L, tb, cYh, cH, cTh, net_ans, net_tag, use_net, T,
-                                              invTf, l, cpp);
-
   // production rates, dY/dt, dT/dt terms and the limiter (FP32)
   const float invRho = 1.0f / rho;
   float hwp = 0.0f, tmin = __int_as_float(0x7f800000);  // +inf
@@ -400,8 +353,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
   }
   const float hw = group_sum<G>(hwp);
   tmin = group_min<G>(tmin);
-  float dTdt = 0.0f;
-  if (!MLP) dTdt = -(Tf * hw) / (rho * cpsum);
+  const float dTdt = -(Tf * hw) / (rho * cpsum);
   // h = min(tmin, t_f delta_max), the last step ends at t_f: decided in FP64
   // as in the FP64 path (all >= 0, so the comparisons run on the bit
   // patterns); h as a float pair for the update
@@ -466,14 +418,6 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     st.nhist += 1;
   }
 
-  if (MLP) {
-    // cp/R only: its network answer is first needed here, which leaves the
-    // evaluator the rates, the limiter and the damper to answer in
-    if (!L.mlp_h) cpsum = net_thermo<G>(L, tb, cYh, cH, cTh, net_ans, net_tag, use_net, T,
-                                        invTf, l, cpp);
-    dTdt = -(Tf * hw) / (rho * cpsum);
-  }
-
   // forward Euler (Eq. 18) in float pairs
   bool bad = false;
   for (int i = l; i < S; i += G) {
@@ -521,10 +465,12 @@ struct MixedCell {
   float* Q;
   float* Hist;
   float* Rof;
-  float* Th;  // network outputs (network kernel only)
 };
 
-__device__ __forceinline__ MixedCell mixed_cell(const Launch& L, unsigned char* base) {
+// net: the cell of a network kernel (its rate array also holds the network's
+// activations and outputs, mixed_q_len).
+__device__ __forceinline__ MixedCell mixed_cell(const Launch& L, unsigned char* base,
+                                                bool net) {
   MixedCell c;
   c.G2 = reinterpret_cast<float2*>(base);  // S + 1 (the unused-slot entry)
   c.Yh = reinterpret_cast<float*>(c.G2 + mS(L) + 1);
@@ -532,9 +478,8 @@ __device__ __forceinline__ MixedCell mixed_cell(const Launch& L, unsigned char* 
   c.C = c.Yl + mS(L);                        // S + 1
   c.H = c.C + mS(L) + 1;
   c.Q = c.H + mS(L);
-  c.Hist = c.Q + mR(L);                      // [Rrev][N | 1]
+  c.Hist = c.Q + mixed_q_len(mS(L), mR(L), net);  // [Rrev][N | 1]
   c.Rof = c.Hist + (L.dft_n | 1) * mRrev(L);
-  c.Th = c.Rof + mRrev(L);
   return c;
 }
 
@@ -664,20 +609,26 @@ __device__ __forceinline__ void store_mixed_cell(const Launch& L, int l, MixedCe
   st.cell = -1;
 }
 
-// Mixed-precision persistent kernel, NASA-7 thermo: lane groups of G lanes,
-// one cell each, refilled in place (Sec. 2.4).
-template <int G, int NT>
-__global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// The mixed-precision persistent kernels' body: lane groups of G lanes, one
+// cell each, refilled in place (Sec. 2.4); MLP: with the thermo network
+// evaluated by each warp for its cells inside the step (Sec. 3).
+// Shared memory: tables | cells (blockDim / G blocks of cell_bytes).
+template <int G, int NT, bool MLP>
+__device__ __forceinline__ void mixed_kernel_body(const Launch& L, unsigned char* smem_raw) {
   const int S = mS(L);
   const TablesF tb = stage_tables_mixed(L, smem_raw);
 
   const int group = threadIdx.x / G;
   const int l = threadIdx.x % G;
   const size_t tables = table_smem_bytes_mixed(S, mR(L), L.n_gather, L.n_hi_bins, L.dft_n, mGeneral(L));
-  const size_t cell_bytes = cell_smem_bytes_mixed(S, mR(L), mRrev(L), L.dft_n, false);
-  MixedCell cs = mixed_cell(L, smem_raw + tables + (size_t)group * cell_bytes);
+  const size_t cell_bytes = cell_smem_bytes_mixed(S, mR(L), mRrev(L), L.dft_n, MLP);
+  MixedCell cs = mixed_cell(L, smem_raw + tables + (size_t)group * cell_bytes, MLP);
   init_mixed_cell<G>(L, cs, l);
+  // the network's scratch of the warp's first cell (the others follow at
+  // cell_bytes strides)
+  const int warp = threadIdx.x >> 5;
+  float* net_q0 = mixed_cell(L, smem_raw + tables + (size_t)(warp * (32 / G)) * cell_bytes, MLP).Q;
+  const int cell_ld = (int)(cell_bytes / sizeof(float));
 
   const unsigned long long n = (unsigned long long)L.n_cells;
   CellState st = idle_cell_state();
@@ -713,153 +664,26 @@ __global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L)
     }
     idle_since = 0;
     idle_sleep = 1000u;
-    const int outcome = step_mixed<G, false, NT>(L, tb, cs.Yh, cs.Yl, cs.G2, cs.C, cs.H, cs.Q,
-                                             cs.Hist, cs.Rof, Pf, l, st, nullptr, nullptr, 0);
+    const int outcome = step_mixed<G, MLP, NT>(L, tb, cs.Yh, cs.Yl, cs.G2, cs.C, cs.H, cs.Q,
+                                               cs.Hist, cs.Rof, Pf, l, st, net_q0, cell_ld);
     if (st.cell >= 0 && outcome >= 0) store_mixed_cell<G>(L, l, cs, st, outcome);
   }
 }
 
-// Mixed-precision persistent kernel with the thermo network (Sec. 3): one
-// cell per warp (G = 32) in warps 0 .. net_cells-1, and one or two evaluator
-// warps (the last), each running the network on a 16-row MMA tile for its
-// half of the cells:
-//   - a cell warp, at the start of a step whose T is inside the network's
-//     range, publishes its scaled T and then a new request tag in shared
-//     memory, takes the step's rates, and waits for its answer tag only
-//     where cp/R is first needed (the temperature equation);
-//   - an evaluator polls its rows; once 3/4 of them have fresh requests, or
-//     the oldest has waited 4 us, it evaluates all of them (a row without a
-//     new request gets the same values again for its unchanged T), writes the
-//     cells' output rows, and answers by copying the request tags it read;
-//   - the evaluators leave when every cell warp has left.
-// Cell warps never wait for one another, and the network's 48 MMAs serve 16
-// cells.  Tags go after the data they cover (fence in between) and are read
-// before it.
-template <int NT>
-__global__ void __launch_bounds__(kMaxBlockMixedNet, 1) stev_mixed_net_kernel(Launch L) {
+// Mixed-precision persistent kernel, NASA-7 thermo.
+template <int G, int NT>
+__global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int S = mS(L);
-  const TablesF tb = stage_tables_mixed(L, smem_raw);
-  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int ncells = L.net_cells;  // <= 32
-  const int nev = net_evaluators(ncells);
-  const int per_ev = (ncells + nev - 1) / nev;  // rows each evaluator answers, <= 16
-  const size_t tables = table_smem_bytes_mixed(S, mR(L), L.n_gather, L.n_hi_bins, L.dft_n, mGeneral(L));
-  const size_t cell_bytes = cell_smem_bytes_mixed(S, mR(L), mRrev(L), L.dft_n, true);
-  unsigned char* cells = smem_raw + tables;
-  float* sT = reinterpret_cast<float*>(cells + (size_t)ncells * cell_bytes);
-  int* tag_req = reinterpret_cast<int*>(sT + 32);
-  int* tag_ans = tag_req + 32;   // then tag_wait at tag_ans + 32: a waiting cell's tag
-  int* tag_wait = tag_ans + 32;
-  float* ev_base = reinterpret_cast<float*>(tag_wait + 32);
-  constexpr int kEvFloats = 16 + 16 * kNetActLd / 2;  // 16 temperatures + the BF16 tile
-  int* s_active = reinterpret_cast<int*>(ev_base + nev * kEvFloats);
-  // cell r's output row is at a fixed offset in its cell block: rows cell_bytes apart
-  const int out_ld = (int)(cell_bytes / sizeof(float));
-  for (int r = threadIdx.x; r < 32; r += blockDim.x) {
-    sT[r] = 0.0f;
-    tag_req[r] = 0;
-    tag_ans[r] = 0;
-    tag_wait[r] = 0;
-  }
-  if (threadIdx.x == 0) *s_active = ncells;
-  __syncthreads();
+  mixed_kernel_body<G, NT, false>(L, smem_raw);
+}
 
-  if (warp >= ncells) {
-    // ---- evaluator e: rows r0 .. r0 + nrow - 1
-    const int e = warp - ncells;
-    const int r0 = e * per_ev, nrow = min(per_ev, ncells - r0);
-    float* t16 = ev_base + e * kEvFloats;
-    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(t16 + 16);
-    float* th0 = mixed_cell(L, cells + (size_t)r0 * cell_bytes).Th;
-    const int r = r0 + (l & 15);
-    const bool mine = l < 16 && l < nrow;
-    unsigned long long first = 0;  // when the oldest unanswered request was seen
-    while (*(volatile int*)s_active > 0) {
-      int req = 0;
-      bool fresh = false, waiting = false;
-      if (mine) {
-        req = *(volatile int*)&tag_req[r];
-        fresh = req != *(volatile int*)&tag_ans[r];
-        waiting = fresh && *(volatile int*)&tag_wait[r] == req;
-      }
-      const int nfresh = __popc(__ballot_sync(0xffffffffu, fresh));
-      if (nfresh == 0) {
-        first = 0;
-        __nanosleep(128);
-        continue;
-      }
-      // batch: wait for 3/4 of the rows, a cell already waiting, or the oldest
-      // request 4 us old (cells ask at the start of a step and need the
-      // answer near its end)
-      const unsigned long long now = __shfl_sync(0xffffffffu, gtimer_ns(), 0);
-      if (first == 0) first = now;
-      if (4 * nfresh < 3 * nrow && !__any_sync(0xffffffffu, waiting) && now - first < 4000) {
-        __nanosleep(128);
-        continue;
-      }
-      first = 0;
-      __threadfence_block();  // the tags before the temperatures they cover
-      if (l < 16) t16[l] = mine ? *(volatile float*)&sT[r] : 0.0f;
-      __syncwarp();
-      mlp_eval_warp16(L.mlp, t16, act, th0, out_ld, nrow, 0, L.mlp_needed);
-      __threadfence_block();  // the outputs before their answers
-      if (fresh) *(volatile int*)&tag_ans[r] = req;
-    }
-    return;
-  }
-
-  // ---- cell warps
-  MixedCell cs = mixed_cell(L, cells + (size_t)warp * cell_bytes);
-  init_mixed_cell<32>(L, cs, l);
-  const unsigned long long n = (unsigned long long)L.n_cells;
-  CellState st = idle_cell_state();
-  float Pf = (float)kPatm;
-  unsigned long long idle_since = 0;
-  bool idle_committed = false;
-  unsigned idle_sleep = 1000u;
-  int serve_skip = 0;
-  bool exhausted = false;
-  int tag = 0;
-  while (true) {
-    long long c = -1;
-    if (!L.serve) {
-      c = refill<32>(L.counter, n, st.cell < 0, exhausted);
-    } else if (serve_skip > 0) {
-      --serve_skip;
-    } else if (!idle_committed) {
-      bool none_ready;
-      c = serve_refill<32>(L, st.cell < 0, none_ready);
-      if (none_ready) serve_skip = 32;
-    }
-    if (c >= 0) load_mixed_cell<32>(L, c, l, cs, st, Pf);
-    __syncwarp();
-    if (st.cell < 0) {
-      if (!L.serve) break;
-      if (serve_idle(L, idle_since, idle_committed)) break;
-      __nanosleep(idle_sleep);
-      idle_sleep = min(2u * idle_sleep, 32000u);
-      serve_skip = 0;
-      continue;
-    }
-    idle_since = 0;
-    idle_sleep = 1000u;
-    if (in_net_range(st.Th)) {
-      ++tag;  // warp-uniform
-      if (l == 0) {
-        *(volatile float*)&sT[warp] = (st.Th - kTMid) / kTHalf;
-        __threadfence_block();
-        *(volatile int*)&tag_req[warp] = tag;
-      }
-      __syncwarp();
-    }
-    const int outcome = step_mixed<32, true, NT>(L, tb, cs.Yh, cs.Yl, cs.G2, cs.C, cs.H, cs.Q,
-                                             cs.Hist, cs.Rof, Pf, l, st, cs.Th,
-                                             tag_ans + warp, tag);
-    if (outcome >= 0) store_mixed_cell<32>(L, l, cs, st, outcome);
-  }
-  __syncwarp();
-  if (l == 0) atomicSub(s_active, 1);
+// Mixed-precision persistent kernel with the thermo network (Sec. 3): cp/R
+// (and with L.mlp_h H/RT) from the network, evaluated on the tensor cores by
+// each warp for its own cells at the start of every step.
+template <int G, int NT>
+__global__ void __launch_bounds__(kMaxBlockMixed, 1) stev_mixed_net_kernel(Launch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mixed_kernel_body<G, NT, true>(L, smem_raw);
 }
 
 }  // namespace stev

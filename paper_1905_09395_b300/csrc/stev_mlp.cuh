@@ -7,19 +7,30 @@
 // Parameters are one flat FP32 array in the order W1[64], b1[64], W2[64][64],
 // b2[64], W3[3S][64], b3[3S] (rows = outputs).
 //
-// Training (FP32, off the hot path): one fused kernel per minibatch computes
-// the forward pass, the mean-squared-error gradient and the weight gradients
-// of a 64-sample tile entirely in shared memory and adds them to a global
-// gradient buffer; an Adam kernel then updates the parameters.
+// Training (FP32, off the hot path): the forward pass, the mean-squared-error
+// gradient and the weight gradients of a 64-sample tile are computed entirely
+// in shared memory by one CTA and written as the tile's partial gradient; one
+// cooperative launch runs every Adam step (tiles, grid barrier, update, grid
+// barrier).
 // Inference (BF16 weights and activations, FP32 accumulation): warp-level
-// tensor-core MMAs m16n8k16 on 16 temperatures at a time.
+// tensor-core MMAs m16n8k16, on 16 temperatures at a time (batched
+// evaluation) or on the cells of one warp inside the solver's step.
 #pragma once
+#ifndef __CUDACC_RTC__  // the trainer is not part of the run-time compiled solver
+#include <cooperative_groups.h>
+#endif
 #include <cuda_bf16.h>
 #include "stev_device.cuh"
 
 namespace stev {
 
 constexpr int kHid = 64;
+
+#ifndef __CUDACC_RTC__
+// Grid-wide barrier of a cooperative launch (every CTA resident, so it cannot
+// deadlock), with the memory ordering of a release / acquire at GPU scope.
+__device__ __forceinline__ void grid_barrier() { cooperative_groups::this_grid().sync(); }
+#endif
 constexpr float kTMid = 1650.0f, kTHalf = 1350.0f;
 constexpr int kMlpTile = 64;  // samples per CTA in training
 
@@ -118,14 +129,16 @@ __global__ void mlp_standardise_kernel(float* __restrict__ v, long long n, int m
 // [64][tile+1] and dy [n_out][tile+1] (the +1 keeps rows on distinct banks).
 // Writes the tile's d loss / d params to part[blockIdx.x][params] and its sum
 // of squared errors to loss_part[blockIdx.x] (the loss is the mean over
-// n_total samples and n_out outputs); mlp_adam_kernel / mlp_sum_kernel add
+// n_total samples and n_out outputs); mlp_train_kernel / mlp_sum_kernel add
 // the tiles in order, so training is reproducible run to run.
-__global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
+// The tile's work as a device function: tile `tile` of the n samples, shared
+// memory sm (mlp_grad_smem_bytes) and se_w (kMlpTile / 32 doubles).  The
+// parameters are read around L1 (__ldcg): the persistent trainer rewrites
+// them between tiles.
+__device__ __forceinline__ void mlp_grad_tile(
     const float* __restrict__ params, int n_out, const double* __restrict__ T,
     const float* __restrict__ target, long long n, long long n_total, float* __restrict__ part,
-    double* __restrict__ loss_part) {
-  __shared__ double se_w[kMlpTile / 32];
-  extern __shared__ __align__(16) float sm[];
+    double* __restrict__ loss_part, int tile, float* sm, double* se_w) {
   const MlpOffsets off = mlp_offsets(n_out);
   float* P = sm;
   const int ld = kMlpTile + 1;
@@ -135,8 +148,8 @@ __global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
   float* z2 = z1 + kHid * ld;   // dz2
   float* dy = z2 + kHid * ld;   // [n_out][ld]
   float* ts = dy + n_out * ld;  // [tile]
-  for (int k = threadIdx.x; k < off.total; k += blockDim.x) P[k] = params[k];
-  const long long s0 = (long long)blockIdx.x * kMlpTile;
+  for (int k = threadIdx.x; k < off.total; k += blockDim.x) P[k] = __ldcg(params + k);
+  const long long s0 = (long long)tile * kMlpTile;
   const int s = threadIdx.x;
   const bool valid = s0 + s < n;
   __syncthreads();
@@ -178,7 +191,7 @@ __global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kMlpTile / 32; ++w) t += se_w[w];
-    loss_part[blockIdx.x] = t;
+    loss_part[tile] = t;
   }
 
   // weight gradients: sums over the tile's samples
@@ -204,8 +217,18 @@ __global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
       const int o = k - off.b3;
       for (int q = 0; q < nt; ++q) acc += dy[o * ld + q];
     }
-    part[(size_t)blockIdx.x * off.total + k] = acc;
+    part[(size_t)tile * off.total + k] = acc;
   }
+  __syncthreads();  // the tile's shared memory is reused by the caller's next tile
+}
+
+__global__ void __launch_bounds__(kMlpTile) mlp_grad_kernel(
+    const float* __restrict__ params, int n_out, const double* __restrict__ T,
+    const float* __restrict__ target, long long n, long long n_total, float* __restrict__ part,
+    double* __restrict__ loss_part) {
+  __shared__ double se_w[kMlpTile / 32];
+  extern __shared__ __align__(16) float sm[];
+  mlp_grad_tile(params, n_out, T, target, n, n_total, part, loss_part, blockIdx.x, sm, se_w);
 }
 
 // grad[k] = sum over tiles of part[tile][k], tiles in order; thread 0 also
@@ -230,69 +253,127 @@ __host__ __device__ inline size_t mlp_grad_smem_bytes(int n_out) {
          sizeof(float);
 }
 
-// Adam (Kingma & Ba 2015) on every parameter, the gradient being the sum of
-// the minibatch's tile partials (in tile order); thread 0 adds the tiles'
-// squared errors to *loss_acc.
-__global__ void mlp_adam_kernel(float* __restrict__ p, const float* __restrict__ part, int tiles,
-                                const double* __restrict__ loss_part, double* __restrict__ loss_acc,
-                                float* __restrict__ m1, float* __restrict__ m2, int n, float lr,
-                                float beta1, float beta2, float eps, float bc1, float bc2) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0) {
-    double t = 0.0;
-    for (int b = 0; b < tiles; ++b) t += loss_part[b];
-    *loss_acc += t;
+#ifndef __CUDACC_RTC__
+// Every Adam step (Kingma & Ba 2015) of a training run in one cooperative
+// launch (all CTAs resident; grid-wide barriers between the phases).  Per
+// step: the minibatch's tiles (grid-stride over CTAs, each tile by
+// mlp_grad_tile), a barrier, then Adam on every parameter, its gradient the
+// sum of the tile partials in tile order (one thread adds the tiles' squared
+// errors, in order, to the epoch's loss), a barrier.  sched[step] = (step
+// size, 1 - b1^t, 1 - b2^t) as the host computes them.  The same inputs train
+// the same network bit for bit.  Reads of data other CTAs wrote go around L1.
+__global__ void __launch_bounds__(kMlpTile) mlp_train_kernel(
+    float* __restrict__ p, int n_out, const double* __restrict__ T,
+    const float* __restrict__ target, long long n, int batch, const float4* __restrict__ sched,
+    long long steps, long long per_epoch, float* __restrict__ part, double* __restrict__ loss_part,
+    float* __restrict__ m1, float* __restrict__ m2, double* __restrict__ loss_epoch, float beta1,
+    float beta2, float eps) {
+  __shared__ double se_w[kMlpTile / 32];
+  extern __shared__ __align__(16) float sm[];
+  const int np = mlp_n_params(n_out);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  for (long long step = 0; step < steps; ++step) {
+    const long long ep = step / per_epoch;
+    const long long s0 = (step - ep * per_epoch) * batch;
+    const long long nb = min((long long)batch, n - s0);
+    const int tiles = (int)((nb + kMlpTile - 1) / kMlpTile);
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x)
+      mlp_grad_tile(p, n_out, T + s0, target + s0 * n_out, nb, nb, part, loss_part, t, sm, se_w);
+    grid_barrier();
+    const float4 sc = sched[step];
+    if (gtid == 0) {
+      double acc = 0.0;
+      for (int b = 0; b < tiles; ++b) acc += __ldcg(loss_part + b);
+      loss_epoch[ep] += acc;
+    }
+    for (long long k = gtid; k < np; k += nthreads) {
+      float gk = 0.0f;
+      for (int b = 0; b < tiles; ++b) gk += __ldcg(part + (size_t)b * np + k);
+      const float a = beta1 * m1[k] + (1.0f - beta1) * gk;
+      const float bb = beta2 * m2[k] + (1.0f - beta2) * gk * gk;
+      m1[k] = a;
+      m2[k] = bb;
+      p[k] -= sc.x * (a / sc.y) / (sqrtf(bb / sc.z) + eps);
+    }
+    grid_barrier();
   }
-  if (k >= n) return;
-  float gk = 0.0f;
-  for (int b = 0; b < tiles; ++b) gk += part[(size_t)b * n + k];
-  const float a = beta1 * m1[k] + (1.0f - beta1) * gk;
-  const float b = beta2 * m2[k] + (1.0f - beta2) * gk * gk;
-  m1[k] = a;
-  m2[k] = b;
-  p[k] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
 }
+#endif
 
 // --------------------------------------- Levenberg-Marquardt (Sec. 3)
-// Jacobian of the standardised outputs with respect to every parameter, one
-// CTA of kHid threads per sample, and the residuals y - target.  Row
-// s * n_out + o of J (n_params floats, the flattened parameter order) is
-//   W1[k]: d1_k t,  b1[k]: d1_k,  W2[j][k]: d2_j a1_k,  b2[j]: d2_j,
-//   W3[o'][k]: a2_k if o' == o else 0,  b3[o']: 1 if o' == o else 0,
-// with d2_j = W3[o][j] (1 - a2_j^2) and d1_k = (1 - a1_k^2) sum_j W2[j][k] d2_j.
-__global__ void __launch_bounds__(kHid) mlp_jacobian_kernel(
+// Jacobian of the standardised outputs with respect to every parameter and
+// the residuals y - target, one CTA per sample, written TRANSPOSED: Jt
+// [n_params][ldk], column s * n_out + o holds d y_o(sample s) / d param, so
+// that each parameter's row is contiguous in the samples (the K-major operand
+// of the Gram kernel, and one coalesced segment of n_out values per parameter
+// and sample).  With d2_oj = W3[o][j] (1 - a2_j^2) and
+// d1_ok = (1 - a1_k^2) sum_j W2[j][k] d2_oj the entries are
+//   W1[k]: d1_ok t,  b1[k]: d1_ok,  W2[j][k]: d2_oj a1_k,  b2[j]: d2_oj,
+//   W3[o'][k]: a2_k if o' == o else 0,  b3[o']: 1 if o' == o else 0.
+// Shared memory: a1, a2 [64], d2 and d1 [n_out][64] (mlp_jacobian_smem_bytes).
+constexpr int kJacThreads = 256;
+__host__ __device__ inline size_t mlp_jacobian_smem_bytes(int n_out) {
+  return ((size_t)2 * kHid + (size_t)2 * n_out * kHid) * sizeof(float);
+}
+__global__ void __launch_bounds__(kJacThreads) mlp_jacobian_t_kernel(
     const float* __restrict__ params, int n_out, const double* __restrict__ T,
-    const float* __restrict__ target, float* __restrict__ J, float* __restrict__ resid) {
-  __shared__ float a1[kHid], a2[kHid], d2[kHid];
+    const float* __restrict__ target, float* __restrict__ Jt, long long ldk,
+    float* __restrict__ resid) {
+  extern __shared__ __align__(16) float jsm[];
+  float* a1 = jsm;
+  float* a2 = a1 + kHid;
+  float* d2 = a2 + kHid;               // [n_out][64]
+  float* d1 = d2 + (size_t)n_out * kHid;  // [n_out][64]
   const MlpOffsets off = mlp_offsets(n_out);
-  const int s = blockIdx.x, k = threadIdx.x;
+  const int s = blockIdx.x, tid = threadIdx.x;
   const float t = ((float)T[s] - kTMid) / kTHalf;
-  a1[k] = tanhf(fmaf(params[off.W1 + k], t, params[off.b1 + k]));
+  if (tid < kHid) a1[tid] = tanhf(fmaf(params[off.W1 + tid], t, params[off.b1 + tid]));
   __syncthreads();
-  float acc = params[off.b2 + k];
-  for (int i = 0; i < kHid; ++i) acc = fmaf(params[off.W2 + k * kHid + i], a1[i], acc);
-  a2[k] = tanhf(acc);
+  if (tid < kHid) {
+    float acc = params[off.b2 + tid];
+    for (int i = 0; i < kHid; ++i) acc = fmaf(params[off.W2 + tid * kHid + i], a1[i], acc);
+    a2[tid] = tanhf(acc);
+  }
   __syncthreads();
-  for (int o = 0; o < n_out; ++o) {
-    float* row = J + ((size_t)s * n_out + o) * off.total;
-    if (k == 0) {
-      float y = params[off.b3 + o];
-      for (int j = 0; j < kHid; ++j) y = fmaf(params[off.W3 + o * kHid + j], a2[j], y);
-      resid[(size_t)s * n_out + o] = y - target[(size_t)s * n_out + o];
-    }
-    d2[k] = params[off.W3 + o * kHid + k] * (1.0f - a2[k] * a2[k]);
-    __syncthreads();
+  for (int o = tid; o < n_out; o += blockDim.x) {
+    float y = params[off.b3 + o];
+    for (int j = 0; j < kHid; ++j) y = fmaf(params[off.W3 + o * kHid + j], a2[j], y);
+    resid[(size_t)s * n_out + o] = y - target[(size_t)s * n_out + o];
+  }
+  for (int q = tid; q < n_out * kHid; q += blockDim.x) {
+    const int o = q / kHid, j = q % kHid;
+    d2[q] = params[off.W3 + o * kHid + j] * (1.0f - a2[j] * a2[j]);
+  }
+  __syncthreads();
+  for (int q = tid; q < n_out * kHid; q += blockDim.x) {
+    const int o = q / kHid, k = q % kHid;
     float g = 0.0f;
-    for (int j = 0; j < kHid; ++j) g = fmaf(params[off.W2 + j * kHid + k], d2[j], g);
-    const float d1 = g * (1.0f - a1[k] * a1[k]);
-    row[off.W1 + k] = d1 * t;
-    row[off.b1 + k] = d1;
-    for (int j = 0; j < kHid; ++j) row[off.W2 + j * kHid + k] = d2[j] * a1[k];
-    row[off.b2 + k] = d2[k];
-    for (int q = k; q < n_out * kHid; q += kHid)
-      row[off.W3 + q] = (q / kHid == o) ? a2[q % kHid] : 0.0f;
-    for (int q = k; q < n_out; q += kHid) row[off.b3 + q] = (q == o) ? 1.0f : 0.0f;
-    __syncthreads();
+    for (int j = 0; j < kHid; ++j) g = fmaf(params[off.W2 + j * kHid + k], d2[o * kHid + j], g);
+    d1[q] = g * (1.0f - a1[k] * a1[k]);
+  }
+  __syncthreads();
+  float* col = Jt + (size_t)s * n_out;
+  const long long total = (long long)off.total * n_out;
+  for (long long q = tid; q < total; q += blockDim.x) {
+    const int p = (int)(q / n_out), o = (int)(q % n_out);
+    float v;
+    if (p < off.b1) {
+      v = d1[o * kHid + (p - off.W1)] * t;
+    } else if (p < off.W2) {
+      v = d1[o * kHid + (p - off.b1)];
+    } else if (p < off.b2) {
+      const int j = (p - off.W2) / kHid, k = (p - off.W2) % kHid;
+      v = d2[o * kHid + j] * a1[k];
+    } else if (p < off.W3) {
+      v = d2[o * kHid + (p - off.b2)];
+    } else if (p < off.b3) {
+      const int oo = (p - off.W3) / kHid, k = (p - off.W3) % kHid;
+      v = (oo == o) ? a2[k] : 0.0f;
+    } else {
+      v = (p - off.b3 == o) ? 1.0f : 0.0f;
+    }
+    col[(size_t)p * ldk + o] = v;
   }
 }
 
@@ -321,23 +402,11 @@ __global__ void mlp_sqerr_kernel(const float* __restrict__ params, int n_out,
   se[s] = e;
 }
 
-// A (FP32, n x n, column-major lower part from SYRK) -> Ad (FP64, full lower
-// part) with Marquardt's damping on the diagonal: A_ii (1 + lambda) + eps.
-__global__ void mlp_damp_kernel(const float* __restrict__ A, int n, double lambda, double eps,
-                                double* __restrict__ Ad) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * n) return;
-  const int c = (int)(idx / n), r = (int)(idx % n);
-  double v = r >= c ? (double)A[idx] : 0.0;
-  if (r == c) v = v * (1.0 + lambda) + eps;
-  Ad[idx] = v;
-}
-
-// p_new = p - (float)d
-__global__ void mlp_step_kernel(const float* __restrict__ p, const double* __restrict__ d, int n,
+// p_new = p - d
+__global__ void mlp_step_kernel(const float* __restrict__ p, const float* __restrict__ d, int n,
                                 float* __restrict__ p_new) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) p_new[k] = p[k] - (float)d[k];
+  if (k < n) p_new[k] = p[k] - d[k];
 }
 
 // ------------------------------------------------------------- inference
@@ -358,6 +427,122 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, const unsigned* a, cons
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// m16n8k16 with the A fragment as one 16-byte word per lane (fragment-ordered
+// weights, MlpFrag).
+__device__ __forceinline__ void mma_bf16_16816_a(float* d, uint4 a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b[0]), "r"(b[1]));
+}
+
+// Offsets (32-bit words) in a cell's network scratch: layer-1 activations
+// (64 BF16), layer-2 activations (64 BF16), then the outputs (FP32 rows).
+constexpr int kNetH1Off = 0, kNetH2Off = 32, kNetOutOff = 64;
+
+// The network of every cell a warp holds, inside the solver's step (Sec. 3:
+// the network stands in for the NASA-7 evaluation).  The warp holds CPW =
+// 32 / G cells (lane groups of G); column c of the MMAs' B operand carries
+// cell c mod CPW, and the weights are the A operand (16 output units per
+// tile), so a cell's layer 2 is 16 MMAs and each 16 output rows of layer 3
+// four more, whatever CPW.  t: this lane's cell's scaled temperature
+// (T - 1650) / 1350.  q0: the network scratch of the warp's first cell
+// (kNet*Off), cell k's at q0 + k * cell_ld (32-bit words); rows
+// 0 .. n_rows - 1 of each cell's outputs (cp/R of each species, then H/R)
+// are written, with the rest of their 16-row tile (mixed_q_len leaves room).
+// Warp-collective.
+template <int G>
+__device__ __forceinline__ void net_eval_cells(const MlpFrag& f, float t, float* q0, int cell_ld,
+                                               int n_rows) {
+  constexpr int CPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, q = lane & 3;
+  unsigned* w0 = reinterpret_cast<unsigned*>(q0);
+  // layer 1 (1 -> 64, FP32 FMA and tanh): lane l of cell k takes hidden units
+  // l, l + G, ...
+  {
+    __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(w0 + (lane / G) * cell_ld + kNetH1Off);
+#pragma unroll
+    for (int u = 0; u < kHid / G; ++u) {
+      const int j = lane % G + G * u;
+      const float2 wb = f.w1[j];
+      h1[j] = __float2bfloat16_rn(tanh_approx(fmaf(wb.x, t, wb.y)));
+    }
+  }
+  __syncwarp();
+  // B fragments: column g is cell g mod CPW; rows (hidden inputs) 2q, 2q + 1
+  // and 2q + 8, 2q + 9 of each 16-row k-tile
+  const unsigned* hb = w0 + (g % CPW) * cell_ld;
+  unsigned b[4][2];
+#pragma unroll
+  for (int kt = 0; kt < 4; ++kt) {
+    b[kt][0] = hb[kNetH1Off + kt * 8 + q];
+    b[kt][1] = hb[kNetH1Off + kt * 8 + 4 + q];
+  }
+  // layer 2 (64 -> 64): D[j][c] = sum_i W2[j][i] h1_c[i] + b2[j], four m-tiles
+  float d[4][4];
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt) {
+    const float2 bb = f.b2[mt * 32 + lane];
+    d[mt][0] = bb.x;
+    d[mt][1] = bb.x;
+    d[mt][2] = bb.y;
+    d[mt][3] = bb.y;
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) mma_bf16_16816_a(d[mt], __ldg(f.W2 + (mt * 4 + kt) * 32 + lane), b[kt]);
+  }
+  // tanh into the cells' layer-2 activations: lane (g, q) holds rows
+  // 16 mt + g and 16 mt + g + 8 of columns 2q and 2q + 1, i.e. of cells
+  // (2q + half) mod CPW.  Lanes whose columns repeat the same cells split the
+  // m-tiles between them, so that each activation is computed once: with one
+  // cell per warp lane (g, q) takes m-tile q; with two cells, m-tile q of both;
+  // with four, m-tiles 2 (q / 2) and 2 (q / 2) + 1 of its two cells.
+  {
+    constexpr int kMtPerLane = CPW == 1 ? 1 : (CPW == 2 ? 1 : 2);
+    constexpr int kHalves = CPW == 1 ? 1 : 2;
+    const int mt0 = CPW == 4 ? 2 * (q >> 1) : q;
+#pragma unroll
+    for (int u = 0; u < kMtPerLane; ++u) {
+      const int mt = mt0 + u;
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)  // d[mt][e] with mt known per lane only at run time
+        v[e] = mt == 0 ? d[0][e] : mt == 1 ? d[1][e] : mt == 2 ? d[2][e] : d[3][e];
+#pragma unroll
+      for (int half = 0; half < kHalves; ++half) {
+        __nv_bfloat16* h2 = reinterpret_cast<__nv_bfloat16*>(
+            w0 + ((2 * q + half) % CPW) * cell_ld + kNetH2Off) + mt * 16 + g;
+        h2[0] = __float2bfloat16_rn(tanh_approx(v[half]));
+        h2[8] = __float2bfloat16_rn(tanh_approx(v[2 + half]));
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int kt = 0; kt < 4; ++kt) {
+    b[kt][0] = hb[kNetH2Off + kt * 8 + q];
+    b[kt][1] = hb[kNetH2Off + kt * 8 + 4 + q];
+  }
+  // layer 3 (64 -> outputs), the m-tiles holding rows below n_rows (whole
+  // tiles are written: the output rows have room for them); the bias and the
+  // standardisation are folded into (scale, offset)
+  const int n_mt = (n_rows + 15) >> 4;
+  for (int mt = 0; mt < n_mt; ++mt) {
+    float e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) mma_bf16_16816_a(e, __ldg(f.W3 + (mt * 4 + kt) * 32 + lane), b[kt]);
+    const float4 so = f.o3[mt * 32 + lane];
+#pragma unroll
+    for (int half = 0; half < (CPW > 1 ? 2 : 1); ++half) {
+      float* out = q0 + ((2 * q + half) % CPW) * cell_ld + kNetOutOff + mt * 16 + g;
+      out[0] = fmaf(e[half], so.x, so.y);
+      out[8] = fmaf(e[2 + half], so.z, so.w);
+    }
+  }
+  __syncwarp();
 }
 
 // One warp evaluates the network at 16 temperatures (rows).  act is a warp-

@@ -47,7 +47,7 @@ std::string cuda_include_dir() {
 std::string kernel_name(const SpecKey& k) {
   char buf[96];
   if (k.net)
-    std::snprintf(buf, sizeof buf, "stev::stev_mixed_net_kernel<%d>", k.NT);
+    std::snprintf(buf, sizeof buf, "stev::stev_mixed_net_kernel<%d, %d>", k.G, k.NT);
   else
     std::snprintf(buf, sizeof buf, "stev::stev_mixed_kernel<%d, %d>", k.G, k.NT);
   return buf;
@@ -129,9 +129,8 @@ extern "C" stev_status stev_spec_compile_check(int n_species, int n_reactions, i
   if (n_species < 1 || n_species > 64 || n_reactions < 1 || n_reactions > 512 ||
       n_reversible < 0 || n_reversible > n_reactions)
     return stev::host::fail(STEV_EINVAL, "sizes out of range");
-  if (!(lanes_per_cell == 8 || lanes_per_cell == 16 || lanes_per_cell == 32) ||
-      (network && lanes_per_cell != 32))
-    return stev::host::fail(STEV_EINVAL, "lanes_per_cell must be 8, 16 or 32 (32 with the network)");
+  if (!(lanes_per_cell == 8 || lanes_per_cell == 16 || lanes_per_cell == 32))
+    return stev::host::fail(STEV_EINVAL, "lanes_per_cell must be 8, 16 or 32");
   stev::host::SpecKey k{n_species, n_reactions, n_reversible, general ? 1 : 0, lanes_per_cell,
                         dft_n == 13 ? 13 : 0, network ? 1 : 0};
   std::vector<char> cubin;

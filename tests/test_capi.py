@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 def declared_symbols():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(stev_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(stev_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_and_binding_agree():

@@ -13,6 +13,8 @@ from paper_1905_09395_b300 import binding
     (32, 150, 150, False, 32, 13, False),   # the 32/150 workload
     (32, 150, 150, False, 32, 13, True),    # ... with the thermo network
     (8, 20, 20, False, 8, 13, False),       # the 8/20 mechanism, 4 cells per warp
+    (8, 20, 20, False, 8, 13, True),        # ... with the network, 4 cells per warp
+    (6, 2, 1, True, 8, 13, True),           # BFER with the network
     (53, 325, 325, False, 32, 13, False),   # 53/325, two species per lane
     (6, 2, 1, True, 8, 13, False),          # BFER: real orders and stoichiometry
     (16, 40, 40, False, 16, 9, False),      # a run-time window length
@@ -26,4 +28,4 @@ def test_bad_sizes_are_rejected():
     with pytest.raises(binding.StevError):
         binding.spec_compile_check(65, 10, 10)
     with pytest.raises(binding.StevError):
-        binding.spec_compile_check(32, 150, 150, lanes_per_cell=16, network=True)
+        binding.spec_compile_check(32, 150, 150, lanes_per_cell=4, network=True)
