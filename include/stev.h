@@ -211,6 +211,35 @@ stev_status stev_solve_host_noalloc(stev_mechanism *mech, long n_cells, const do
                                     double *T_out, double *Y_out, int *iters,
                                     unsigned char *cell_status, void *cuda_stream);
 
+/* ---- multiphase coal gasification cells (Sec. 7.2: reactions 31-41, rate laws
+ * Eqs. 42-56, Table 2) integrated by STEV (Eqs. 1-5, 8-14, 18), FP64.
+ *   cells      [n_cells][24] DEVICE records: gas mass fractions of O2 CO CO2
+ *              CH4 H2 H2O H2S C3H6 HCN C2H4 C2H6 Tar SO3 N2 (14), solid mass
+ *              fractions of CV (volatile matter) CC (fixed carbon) CM
+ *              (moisture) CA (ash) (4), T_g, T_s (K), eps_s (solid volume
+ *              fraction), rho_s (solid material density, kg/m^3), d_p
+ *              (particle diameter, m), P (Pa).  With eps_g = 1 - eps_s and
+ *              rho_g (the ideal gas law at P, T_g and the gas's molar mass)
+ *              these are the paper's 26 variables per cell.
+ *   dt_cfd     the fluid step t_f (s).
+ *   opt        NULL = defaults; y_step_max, delta_max, alpha, dft_n,
+ *              dft_hi_first, tol_ring, tol_freq, r_fac, rof_min, max_iters and
+ *              dft_on are used (precision, thermo, lanes and specialize are
+ *              not: the path is FP64).
+ *   cells_out  [n_cells][24] DEVICE: the records after t_f: new mass
+ *              fractions and eps_s; T_g, T_s, rho_s, d_p, P as given (the
+ *              phase temperatures are held over the chemistry step: the
+ *              paper prints no phase energy equations).  May equal cells.
+ *   rho_g      [n_cells] DEVICE (nullable): the final gas density.
+ *   iters, cell_status [n_cells] DEVICE, as stev_solve.
+ * The species' partial densities are integrated (mass is conserved by the
+ * reactions, read as molar with Tar's and CV's molecular weights balancing
+ * Eqs. 37 and 31, rates of progress in kmol/m^3/s); eps_s follows the solid's
+ * mass at constant rho_s.  Asynchronous on cuda_stream. */
+stev_status stev_mp_solve(long n_cells, const double *cells, double dt_cfd,
+                          const stev_options *opt, double *cells_out, double *rho_g, int *iters,
+                          unsigned char *cell_status, void *cuda_stream);
+
 /* ---- thermo network (Sec. 3: a small neural network of temperature stands in
  * for the NASA-7 species properties; Figs. 2-3).  The library's network is
  * t = (T - 1650)/1350, a1 = tanh(W1 t + b1), a2 = tanh(W2 a1 + b2) (64 each),

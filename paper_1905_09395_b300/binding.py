@@ -33,6 +33,7 @@ EXPORTS = (
     "stev_server_clock", "stev_server_stop", "stev_server_destroy", "stev_mlp_stalls",
     "stev_mlp_train_lm", "stev_mlp_jacobian", "stev_mechanism_create_orders",
     "stev_is_specialized", "stev_spec_compile_check", "stev_gram_tf32", "stev_damped_cg",
+    "stev_mp_solve",
 )
 
 
@@ -108,6 +109,8 @@ def lib():
         L.stev_mlp_train_lm.restype = I
         L.stev_mlp_jacobian.argtypes = [P, P, P, LNG, P]
         L.stev_mlp_jacobian.restype = I
+        L.stev_mp_solve.argtypes = [LNG, P, D, P, P, P, P, P, P]
+        L.stev_mp_solve.restype = I
         L.stev_gram_tf32.argtypes = [LNG, LNG, P, LNG, P, LNG, P]
         L.stev_gram_tf32.restype = I
         L.stev_damped_cg.argtypes = [LNG, P, LNG, P, ctypes.c_double, ctypes.c_double, P,
@@ -479,6 +482,25 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def mp_solve(cells, dt: float, out=None, stream=None, **options):
+    """Multiphase coal gasification cells (stev_mp_solve, Sec. 7.2): cells is a
+    CUDA float64 tensor [n][24]; returns (cells_out, rho_g, iters, status)."""
+    import torch
+    n = int(cells.shape[0])
+    if tuple(cells.shape) != (n, 24) or cells.dtype != torch.float64 or not cells.is_cuda:
+        raise ValueError("cells must be a CUDA float64 tensor of shape [n, 24]")
+    cells = cells.contiguous()
+    if out is None:
+        out = (torch.empty_like(cells), torch.empty(n, dtype=torch.float64, device=cells.device),
+               torch.empty(n, dtype=torch.int32, device=cells.device),
+               torch.empty(n, dtype=torch.uint8, device=cells.device))
+    o = default_options(**options)
+    _check(lib().stev_mp_solve(n, cells.data_ptr(), float(dt), ctypes.byref(o), out[0].data_ptr(),
+                               out[1].data_ptr(), out[2].data_ptr(), out[3].data_ptr(),
+                               _stream_handle(stream)))
+    return out
 
 
 def gram_tf32(X, k: Optional[int] = None, stream=None):

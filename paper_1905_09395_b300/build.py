@@ -34,7 +34,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                "--expt-relaxed-constexpr", "-Xptxas", "-v" if verbose else "-O3",
                "-o", tmp, os.path.join(CSRC, "stev_capi.cu"),
                os.path.join(CSRC, "stev_server.cu"), os.path.join(CSRC, "stev_spec.cu"),
-               os.path.join(CSRC, "stev_lm.cu"), "-lnvrtc"]
+               os.path.join(CSRC, "stev_lm.cu"), os.path.join(CSRC, "stev_multiphase.cu"),
+               "-lnvrtc"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

@@ -389,3 +389,37 @@ def bfer_cells(mech: Mechanism, n_cells: int, seed: int = 6,
     Y[:, 4] = rng.uniform(0.0, 0.05, n_cells)
     Y[:, 5] = 1.0 - Y[:, :5].sum(axis=1)
     return T, P, Y
+
+
+# ----------------------------------------------------------------------------
+# multiphase cells (Sec. 7.2): random gasifier-like thermochemical states
+# ----------------------------------------------------------------------------
+MP_GAS = ("O2", "CO", "CO2", "CH4", "H2", "H2O", "H2S", "C3H6", "HCN", "C2H4", "C2H6", "Tar",
+          "SO3", "N2")
+MP_SOLID = ("CV", "CC", "CM", "CA")
+
+
+def multiphase_cells(n_cells: int, seed: int = 0, T_range: Tuple[float, float] = (900.0, 1500.0),
+                     o2_max: float = 0.1) -> np.ndarray:
+    """Seeded multiphase cell records [n][24]: gas mass fractions X_g[14]
+    (nitrogen-rich, O2 up to o2_max), solid mass fractions X_s[4] (volatile
+    matter, fixed carbon, moisture, ash), T_g uniform in T_range, T_s within
+    100 K of it, eps_s U[0.02, 0.4], particle density rho_s U[1000, 1500]
+    kg/m^3, d_p U[1e-4, 5e-4] m, P U[1, 5] atm (Pa)."""
+    rng = np.random.default_rng(seed + 104729)
+    gas_a = np.array([1, 1, 1, 0.5, 0.5, 1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 4.0])
+    Xg = rng.dirichlet(gas_a, size=n_cells)
+    o2 = rng.uniform(0.0, o2_max, size=n_cells)
+    Xg[:, 0] = 0.0
+    Xg /= Xg.sum(axis=1, keepdims=True)
+    Xg *= (1.0 - o2)[:, None]
+    Xg[:, 0] = o2
+    Xs = rng.dirichlet(np.array([1.0, 2.0, 0.5, 1.0]), size=n_cells)
+    Tg = rng.uniform(T_range[0], T_range[1], size=n_cells)
+    Ts = Tg + rng.uniform(-100.0, 100.0, size=n_cells)
+    eps = rng.uniform(0.02, 0.4, size=n_cells)
+    rho_s = rng.uniform(1000.0, 1500.0, size=n_cells)
+    dp = rng.uniform(1e-4, 5e-4, size=n_cells)
+    P = rng.uniform(1.0, 5.0, size=n_cells) * P_ATM
+    return np.ascontiguousarray(np.column_stack([Xg, Xs, Tg, Ts, eps, rho_s, dp, P]),
+                                dtype=np.float64)

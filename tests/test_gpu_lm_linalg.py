@@ -43,9 +43,11 @@ def test_gram_within_the_tf32_bound(n, k):
     2^-9 relative; FP32 accumulation of k terms adds k 2^-24 relative per
     term, doubled for slack), and the typical error is far below the bound."""
     rng = np.random.default_rng(7)
-    X = rng.normal(size=(n, k)).astype(np.float32)
-    G = binding.gram_tf32(_dev(X)).cpu().numpy().astype(np.float64)
-    X64 = X.astype(np.float64)
+    ldx = (k + 3) // 4 * 4
+    Xp = np.zeros((n, ldx), np.float32)
+    Xp[:, :k] = rng.normal(size=(n, k))
+    G = binding.gram_tf32(_dev(Xp), k).cpu().numpy().astype(np.float64)
+    X64 = Xp[:, :k].astype(np.float64)
     ref = X64 @ X64.T
     scale = np.abs(X64) @ np.abs(X64).T
     err = np.abs(G - ref)
