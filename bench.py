@@ -49,7 +49,7 @@ N_SMS = 148
 # profiles/ (reads only: the small cases' output writes stay in L2), scaled to
 # the full launch by the cells it processes.  None when the kernel changed
 # after its capture.
-DRAM_BYTES_PER_CELL = {"mixed": 956416 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 939520 / 3108}
+DRAM_BYTES_PER_CELL = {"mixed": 956672 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 1397760 / 3256}
 
 
 def bf16_tflops() -> tuple:
@@ -733,6 +733,115 @@ def run_accuracy(args):
     return 0
 
 
+def run_multiphase(args):
+    """The paper's multiphase workload shape (Sec. 7.2): coal gasification
+    cells (14 gas and 4 solid species, two phase temperatures, 11 reactions
+    with the rate laws of Eqs. 42-56 and Table 2's constants), random
+    gasifier-like states, one FP64 STEV solve of every cell per step
+    (stev_mp_solve); the oracle on a bounded sample beside it."""
+    import torch
+    from paper_1905_09395_b300 import binding, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cells = synth.multiphase_cells(args.cells, seed=7)
+    n = len(cells)
+    d = torch.from_numpy(cells).to(dev)
+    out = (torch.empty_like(d), torch.empty(n, dtype=torch.float64, device=dev),
+           torch.empty(n, dtype=torch.int32, device=dev),
+           torch.empty(n, dtype=torch.uint8, device=dev))
+    for _ in range(args.warmup):
+        binding.mp_solve(d[:min(n, args.warmup_cells)], 1e-3,
+                         out=tuple(x[:min(n, args.warmup_cells)] for x in out))
+    flush = None
+    if cells.nbytes < L2_BYTES:
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev[k][0].record()
+            binding.mp_solve(d, 1e-3, out=out)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    it = out[2].cpu().numpy().astype(np.int64)
+    st = np.bincount(out[3].cpu().numpy(), minlength=4)
+    line = {"metric": "cell-solves/s, multiphase coal gasification cells (Sec. 7.2), FP64",
+            "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "multiphase: 14 gas + 4 solid species, 11 reactions (Eqs. "
+                                   "31-56, Table 2), %d random gasifier-like cells, T_g "
+                                   "U[900,1500] K, dt 1e-3 s" % n,
+                       "l2": l2_note(cells, flushed=flush is not None)},
+            "cell_steps_per_s": float(it.sum()) / (ms / 1e3),
+            "iters": {"mean": float(it.mean()), "p50": float(np.median(it)),
+                      "max": int(it.max())},
+            "cell_status": st.tolist(), "gpu_launches": args.steps,
+            "other_launches_in_timed_region": {"l2_flush": args.steps if flush is not None else 0},
+            "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        from oracle import multiphase as mp
+        cores = os.cpu_count() or 1
+        k = min(n, 65536)
+        t0 = time.time()
+        ref = mp.solve(cells[:k], 1e-3, n_threads=cores)
+        el = time.time() - t0
+        got = out[0][:k].cpu().numpy()
+        dX = np.abs(got[:, :18] - ref[0][:, :18]).max(axis=1)
+        line["cpu_baseline"] = {"value": k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "first %d cells, %.1f s" % (k, el)}
+        line["oracle_error"] = {"cells": k, "max_dX": float(dX.max()),
+                                "within_1e-8": float(np.mean(dX <= 1e-8)),
+                                "status_equal": float(np.mean(out[3][:k].cpu().numpy() == ref[3]))}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gram(args):
+    """The Levenberg-Marquardt trainer's dominant contraction (Sec. 3): the
+    Gauss-Newton matrix G = X X^T of the transposed Jacobian X [rows][K] of
+    the 32/150 network at 512 samples (K = 49,152), TF32 tensor-core products
+    with FP32 accumulation (stev_gram_tf32), timed with CUDA events."""
+    import torch
+    from paper_1905_09395_b300 import binding
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    X = torch.randn((args.gram_rows, 49152), dtype=torch.float32, device="cuda", generator=g)
+    for _ in range(args.warmup):
+        binding.gram_tf32(X)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            binding.gram_tf32(X)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n, k = X.shape
+    nt = (n + 127) // 128
+    flops = nt * (nt + 1) / 2 * 128 * 128 * k * 2     # the lower-triangle tiles computed
+    bf16, src = bf16_tflops()
+    peak = bf16 * 1.1 / 2.25                          # TF32 at the nominal TF32:BF16 ratio
+    tf = flops / (ms / 1e3) / 1e12
+    line = {"metric": "TFLOP/s, Gauss-Newton matrix of the LM trainer (TF32 tensor cores)",
+            "value": tf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
+            "config": {"workload": "G = X X^T, X %d x %d FP32 (normal), lower-triangle "
+                                   "128x128 tiles mirrored" % (n, k)},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak, "traffic": None,
+                         "peak_note": "BF16 %s %.1f x 1.1/2.25" % (src, bf16)},
+            "gpu_launches": args.steps, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_1905_09395_b300 import Mechanism, binding
@@ -910,12 +1019,17 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["scale", "uneven", "serve", "bfer", "accuracy"],
+    ap.add_argument("--workload", choices=["scale", "uneven", "serve", "bfer", "accuracy",
+                                           "multiphase", "gram"],
                     default="scale",
                     help="uneven: 64 uneven 53/325 batches in one batched launch; serve: "
                          "the request loop, mixed+MLP and plain FP64; bfer: the paper's "
                          "BFER methane mechanism on random states; accuracy: the GPU paths "
-                         "against the oracle on a seeded subset of the 1M cells")
+                         "against the oracle on a seeded subset of the 1M cells; multiphase: "
+                         "the paper's coal gasification cells (Sec. 7.2); gram: the LM "
+                         "trainer's Gauss-Newton matrix on the tensor cores")
+    ap.add_argument("--gram-rows", type=int, default=10624,
+                    help="gram workload: rows of X (the network's parameters; 10,624 at S=32)")
     ap.add_argument("--oracle-cells", type=int, default=16384,
                     help="accuracy workload: cells the oracle solves")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second")
@@ -958,6 +1072,10 @@ def main(argv=None):
         return run_bfer(args)
     if args.workload == "accuracy":
         return run_accuracy(args)
+    if args.workload == "multiphase":
+        return run_multiphase(args)
+    if args.workload == "gram":
+        return run_gram(args)
     return run_ours(args)
 
 
