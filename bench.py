@@ -52,15 +52,17 @@ N_SMS = 148
 DRAM_BYTES_PER_CELL = {"mixed": 956672 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 1397760 / 3256}
 
 
-def bf16_tflops() -> tuple:
-    """The BF16 dense tensor rate for a kernel timed inside a long step: the
-    sustained cuBLAS figure of MEASURED_PEAKS.json, else the profiling
-    fallback (sustained near 1.4 PFLOP/s)."""
+def bf16_tflops(burst: bool = False) -> tuple:
+    """The BF16 dense tensor rate of MEASURED_PEAKS.json: the sustained cuBLAS
+    figure for a kernel timed inside a long step, the burst one for a kernel
+    timed alone; else the profiling fallback (1.8 PFLOP/s burst, sustained
+    near 1.4)."""
+    key = "bf16_tflops" if burst else "bf16_tflops_sustained"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+            return float(json.load(f)[key]), "measured (%s)" % ("burst" if burst else "sustained")
     except Exception:
-        return 1400.0, "fallback (sustained)"
+        return (1800.0, "fallback (burst)") if burst else (1400.0, "fallback (sustained)")
 
 
 def method_counts(S: int, R: int, net: bool = False) -> dict:
@@ -93,6 +95,28 @@ def bound_s_per_cell_step(S: int, R: int, precision: str, net: bool, mhz: float,
                 c["div"] / (DIV64_PER_CLK * clk) + c["log"] / (LOG64_PER_CLK * clk))
     return (c["flops"] / (2 * FFMA_PER_CLK * clk) +
             (c["exp"] + c["div"] + c["log"]) / (MUFU_PER_CLK * clk) + c["mma"] / (bf16 * 1e12))
+
+
+# The multiphase method's work per cell-step (Sec. 7.2 cells, one STEV
+# iteration), counted from the algorithm with the phase temperatures held:
+# phase totals, mass fractions, eps, rho_g and MW_g (33 adds, 35 divisions);
+# Eqs. 44-46 (~20 flops, 1 division); 19 gamma factors (19 adds, 19
+# divisions); the eleven rate laws (~71 flops, 3 divisions, 11 powers:
+# Eqs. 47, 48, 50 one each, Eq. 52 three, Eq. 53 two, Eq. 55 three, rho_g^1.75
+# shared); production (40 stoichiometric FMAs, 18 molar masses), phase sums
+# and mass-fraction rates (72 flops, 36 divisions); Eqs. 1-5 (54 flops, 18
+# divisions); Eq. 9's window sum (15); Euler (36): about 420 flops, 112
+# divisions and 11 powers (each an exp and a log).
+MP_COUNTS = {"flops": 420, "div": 112, "pow": 11}
+
+
+def mp_bound_s_per_cell_step(mhz: float) -> float:
+    """FP64 bound of one multiphase cell-step: flops on the FP64 pipe,
+    divisions and pow (exp + log) at the rates of CUDA's double routines."""
+    clk = N_SMS * mhz * 1e6
+    c = MP_COUNTS
+    return (c["flops"] / (2 * DFMA_PER_CLK * clk) + c["div"] / (DIV64_PER_CLK * clk) +
+            c["pow"] * (1.0 / (EXP64_PER_CLK * clk) + 1.0 / (LOG64_PER_CLK * clk)))
 
 
 def alu_roofline(precision: str, S: int, R: int, net: bool, cell_steps: float, seconds: float,
@@ -715,7 +739,11 @@ def run_accuracy(args):
     line = {"metric": "error against the FP64 oracle on a seeded subset of the 1M-cell workload",
             "config": {"workload": "syn32x150, %d cells; oracle on %d seeded cells (%d host "
                                    "threads, %.0f s)" % (n, len(idx), cores, ref["s"])},
-            "data": "synthetic", "arms": {}}
+            "data": "synthetic", "arms": {},
+            "cpu_baseline": {"value": len(idx) / ref["s"], "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": "%d seeded cells of the workload, %.0f s" % (len(idx),
+                                                                                   ref["s"])}}
     for name, g in arms.items():
         fp64 = name == "plain_fp64"
         e = oracle_error(g, ref["res"], 1e-8 if fp64 else 1e-4, 1e-6 if fp64 else 0.5)
@@ -783,6 +811,16 @@ def run_multiphase(args):
             "cell_status": st.tolist(), "gpu_launches": args.steps,
             "other_launches_in_timed_region": {"l2_flush": args.steps if flush is not None else 0},
             "clocks": clk.summary()}
+    mhz = line["clocks"]["sm_mhz"] or 2032.0
+    t = mp_bound_s_per_cell_step(mhz)
+    rate = line["cell_steps_per_s"]
+    peak = 2 * DFMA_PER_CLK * N_SMS * mhz * 1e6
+    line["roofline"] = {"bound": "alu", "achieved": rate * t * peak / 1e12, "peak": peak / 1e12,
+                        "unit": "TFLOP/s", "frac": rate * t, "cell_steps_per_s_bound": 1.0 / t,
+                        "counts_per_cell_step": MP_COUNTS, "traffic": None,
+                        "pipe": "fp64 (DFMA %.3f, div %.3f, exp %.3f, log %.3f /clk/SM) x %d SMs "
+                                "x %.0f MHz sampled" % (DFMA_PER_CLK, DIV64_PER_CLK,
+                                                        EXP64_PER_CLK, LOG64_PER_CLK, N_SMS, mhz)}
     if not args.no_cpu_baseline:
         from oracle import multiphase as mp
         cores = os.cpu_count() or 1
@@ -825,7 +863,7 @@ def run_gram(args):
     n, k = X.shape
     nt = (n + 127) // 128
     flops = nt * (nt + 1) / 2 * 128 * 128 * k * 2     # the lower-triangle tiles computed
-    bf16, src = bf16_tflops()
+    bf16, src = bf16_tflops(burst=True)              # a kernel timed alone
     peak = bf16 * 1.1 / 2.25                          # TF32 at the nominal TF32:BF16 ratio
     tf = flops / (ms / 1e3) / 1e12
     line = {"metric": "TFLOP/s, Gauss-Newton matrix of the LM trainer (TF32 tensor cores)",

@@ -221,8 +221,8 @@ static stev_status configure(stev_mechanism* m) {
   const int per_warp = 32 / G;
   cells = (cells / per_warp) * per_warp;
   if (cells < per_warp) return fail(STEV_EINVAL, "mechanism too large for one warp per CTA");
-  const size_t smem = tables + (size_t)cells * per_cell;
-  const int block = cells * G;
+  size_t smem = tables + (size_t)cells * per_cell;
+  int block = cells * G;
   const void* k = reinterpret_cast<const void*>(select_kernel(m->opt.precision, G, m->opt.thermo,
                                                               m->opt.dft_n));
   // a kernel compiled for this mechanism: reused if its key is unchanged; a
@@ -243,6 +243,21 @@ static stev_status configure(stev_mechanism* m) {
   auto drop_new = [&]() {
     if (new_lib) cudaLibraryUnload(new_lib);
   };
+  // a kernel compiled with a smaller launch bound than the block chosen above
+  // holds fewer cells per CTA
+  {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.maxThreadsPerBlock > 0 &&
+        block > fa.maxThreadsPerBlock) {
+      cells = (fa.maxThreadsPerBlock / G) / per_warp * per_warp;
+      if (cells < per_warp) {
+        drop_new();
+        return fail(STEV_EINVAL, "solver kernel's block limit is below one warp");
+      }
+      smem = tables + (size_t)cells * per_cell;
+      block = cells * G;
+    }
+  }
   int per_sm = 0;
   // The attribute belongs to the kernel function, which mechanisms with the
   // same precision, lane group and thermo share: set it to the device's cap

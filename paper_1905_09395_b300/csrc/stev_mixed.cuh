@@ -48,6 +48,30 @@ __device__ __forceinline__ int mRrev(const Launch& L) { return L.Rrev; }
 __device__ __forceinline__ int mGeneral(const Launch& L) { return L.general; }
 #endif
 
+// Running window sums of the damper (Eq. 9's D0 = |sum of the window| and the
+// sum of |x| of its bound) held in registers for the first kWinRegs reactions
+// of each lane, updated by the tap that enters and the tap that leaves and
+// recomputed exactly once per window (every N steps), instead of re-summed
+// from the 13 taps every step.  Only in a kernel compiled for a mechanism
+// whose every reaction is elementary and reversible (history row = reaction),
+// with 32-lane groups and the N = 13 window.
+#if defined(STEV_SPEC_R) && defined(STEV_SPEC_RREV) && defined(STEV_SPEC_GENERAL)
+constexpr bool kSpecAllRev = STEV_SPEC_R == STEV_SPEC_RREV && !STEV_SPEC_GENERAL;
+constexpr int kSpecTrips32 = (STEV_SPEC_R + 31) / 32;  // reactions per lane, 32-lane groups
+#else
+constexpr bool kSpecAllRev = false;
+constexpr int kSpecTrips32 = 1;
+#endif
+template <int G, int NT, bool MLP>
+struct WinRegs {
+  // four reactions per lane with the polynomial thermo; none with the
+  // network, whose MMA fragments leave no registers for them (measured: with
+  // them that kernel spills and gains 1%, the polynomial one gains 7%)
+  static constexpr int cap = MLP ? 0 : 4;
+  static constexpr int n =
+      (kSpecAllRev && G == 32 && NT == 13) ? (kSpecTrips32 < cap ? kSpecTrips32 : cap) : 0;
+};
+
 __device__ __forceinline__ float ex2f(float x) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -185,6 +209,24 @@ __device__ __forceinline__ float lg2f_approx(float x) {
   return r;
 }
 
+// The reverse term kr C_p0 C_p1 of an elementary reaction (Eqs. 29-30):
+// kr = kf 2^x with x = sum nu g2 as a float pair (s, e), TwoSum on the high
+// parts and plain sums of the error terms and low parts, so that the
+// exponent keeps no cancellation loss before its single rounding.
+__device__ __forceinline__ float reverse_term(const float2* cG2, const float* cC, int a0, int a1,
+                                              int p0, int p1, float lg2kf) {
+  const float2 gp0 = cG2[p0], ga0 = cG2[a0], ga1 = cG2[a1], gp1 = cG2[p1];
+  float sx, e, t;
+  two_sum(gp0.x, -ga0.x, sx, t);
+  e = t + (gp0.y - ga0.y);
+  two_sum(sx, -ga1.x, sx, t);
+  e += t - ga1.y;
+  two_sum(sx, gp1.x, sx, t);
+  e += t + gp1.y;
+  const float x = sx + e;
+  return ex2f(lg2kf + x) * cC[p0] * cC[p1];
+}
+
 // MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
 // (Sec. 3) whenever T is inside its training range; outside it, and for G/RT
 // always, the NASA-7 polynomials are used.  The warp evaluates the network of
@@ -202,7 +244,8 @@ template <int G, bool MLP, int NT>
 __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, float* cYh,
                                           float* cYl, float2* cG2, float* cC, float* cH,
                                           float* cQ, float* cHist, float* cRof, float Pf, int l,
-                                          CellState& st, float* netQ0, int cell_ld) {
+                                          CellState& st, float* netQ0, int cell_ld,
+                                          float* win_s, float* win_a) {
   const int S = mS(L), R = mR(L), Rrev = mRrev(L);
   const int N = NT > 0 ? NT : L.dft_n;
   const int NP = N | 1;
@@ -278,6 +321,35 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
   // kr = kf * 2^(x), x = (dG/RT - dN ln(P_atm/RT)) log2 e = sum nu g2, summed
   // exactly
   const int ktap = st.nhist % N;
+  constexpr int kWin = WinRegs<G, NT, MLP>::n;
+  if constexpr (kWin > 0) {
+    // every reaction elementary and reversible, history row r = reaction r:
+    // the tap that leaves the window (written N steps ago) comes off the
+    // running sums here, before the slot takes this step's raw rate
+#pragma unroll
+    for (int j = 0; j < kSpecTrips32; ++j) {
+      const int r = l + G * j;
+      if (r >= R) break;
+      const float4 rx = tb.rxf[r];
+      const int4 ri = tb.ri[r];
+      const int a0 = ri.x & 0xFF, a1 = (ri.x >> 8) & 0xFF;
+      const int p0 = (ri.x >> 16) & 0xFF, p1 = (ri.x >> 24) & 0xFF;
+      const float lg2kf = fmaf(rx.y, lg2Tf, rx.x) - rx.z * invTf;
+      const float q = ex2f(lg2kf) * cC[a0] * cC[a1] - reverse_term(cG2, cC, a0, a1, p0, p1, lg2kf);
+      float rof = 1.0f;
+      if (L.dft_on) {
+        float* slot = cHist + r * NP + ktap;
+        if (j < kWin) {
+          const float xo = *slot;
+          win_s[j] -= xo;
+          win_a[j] -= fabsf(xo);
+        }
+        *slot = q;
+        rof = cRof[r];
+      }
+      cQ[r] = q * rof;
+    }
+  } else {
 #pragma unroll 2  // two reactions per trip (measured)
   for (int r = l; r < R; r += G) {
     const float4 rx = tb.rxf[r];
@@ -313,24 +385,14 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     float q = ex2f(lg2kf) * cC[a0] * cC[a1];
     float rof = 1.0f;
     if (ri.z) {
-      // x = sum nu g2 as a float pair (s, e): TwoSum on the high parts,
-      // plain sums of the error terms and low parts
-      const float2 gp0 = cG2[p0], ga0 = cG2[a0], ga1 = cG2[a1], gp1 = cG2[p1];
-      float sx, e, t;
-      two_sum(gp0.x, -ga0.x, sx, t);
-      e = t + (gp0.y - ga0.y);
-      two_sum(sx, -ga1.x, sx, t);
-      e += t - ga1.y;
-      two_sum(sx, gp1.x, sx, t);
-      e += t + gp1.y;
-      const float x = sx + e;
-      q -= ex2f(lg2kf + x) * cC[p0] * cC[p1];
+      q -= reverse_term(cG2, cC, a0, a1, p0, p1, lg2kf);
       if (L.dft_on) {
         cHist[ri.w * NP + ktap] = q;
         rof = cRof[ri.w];
       }
     }
     cQ[r] = q * rof;
+  }
   }
   __syncwarp();
 
@@ -374,46 +436,91 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     const bool full = (st.nhist + 1 >= N);
     const float tol_freq = L.tol_freq_f, tol_ring = L.tol_ring_f;
     const float r_fac = L.r_fac_f;
-    for (int w = l; w < Rrev; w += G) {
-      float* hw = cHist + w * NP;
-      const float x = hw[ktap] * hf;
-      hw[ktap] = x;
-      float rof = cRof[w];
-      if (full) {
-        // the window sum (storage order) and sum of |x| in one pass
-        float s = 0.0f, a = 0.0f;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          const float v = hw[m];
-          s += v;
-          a += fabsf(v);
-        }
-        const float D0 = fabsf(s);
-        float rstar = r_fac;
-        if (D0 < tol_freq && D0 < tol_ring * a) {
-          const float inv = 1.0f / a;
-          float max2 = 0.0f;
-          for (int bb = 0; bb < L.n_hi_bins; ++bb) {
-            const float* c = tb.tw + bb * 2 * N;
-            float re = 0.0f, im = 0.0f;
+    // Eqs. 10-13 for a full window hw with sum s (storage order) and sum of
+    // |x| a: the high bins only where D0 < Tol_freq and D0 < Tol_ring a
+    // (every |X_j| <= a, so otherwise Eq. 10 cannot hold)
+    auto next_rof = [&](const float* hw, float s, float a, float rof) -> float {
+      const float D0 = fabsf(s);
+      float rstar = r_fac;
+      if (D0 < tol_freq && D0 < tol_ring * a) {
+        const float inv = 1.0f / a;
+        float max2 = 0.0f;
+        for (int bb = 0; bb < L.n_hi_bins; ++bb) {
+          const float* c = tb.tw + bb * 2 * N;
+          float re = 0.0f, im = 0.0f;
 #pragma unroll 1
-            for (int m = 0; m < N; ++m) {  // rare: not unrolled, taps reloaded
-              const float xm = hw[m];
-              re = fmaf(xm, c[m], re);
-              im = fmaf(xm, c[N + m], im);
-            }
-            re *= inv;
-            im *= inv;
-            max2 = fmaxf(max2, fmaf(re, re, im * im));
+          for (int m = 0; m < N; ++m) {  // rare: not unrolled, taps reloaded
+            const float xm = hw[m];
+            re = fmaf(xm, c[m], re);
+            im = fmaf(xm, c[N + m], im);
           }
-          const float d = D0 * inv;
-          if (d * d < tol_ring * tol_ring * max2) rstar = L.inv_r_fac_f;
+          re *= inv;
+          im *= inv;
+          max2 = fmaxf(max2, fmaf(re, re, im * im));
         }
-        rof = fmaxf(fminf(rof * rstar, 1.0f), L.rof_min_f);
-      } else {
-        rof = fminf(rof * r_fac, 1.0f);
+        const float d = D0 * inv;
+        if (d * d < tol_ring * tol_ring * max2) rstar = L.inv_r_fac_f;
       }
-      cRof[w] = rof;
+      return fmaxf(fminf(rof * rstar, 1.0f), L.rof_min_f);
+    };
+    // the window sum (storage order) and sum of |x| in one pass
+    auto window_sums = [&](const float* hw, float& s, float& a) {
+      s = 0.0f;
+      a = 0.0f;
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        const float v = hw[m];
+        s += v;
+        a += fabsf(v);
+      }
+    };
+    if constexpr (kWin > 0) {
+      // exact sums once per window (the first full step and every N steps
+      // after), running sums in between
+      const bool refresh = (st.nhist + 1) % N == 0;
+#pragma unroll
+      for (int j = 0; j < kSpecTrips32; ++j) {
+        const int w = l + G * j;
+        if (w >= Rrev) break;
+        float* hw = cHist + w * NP;
+        const float x = hw[ktap] * hf;
+        hw[ktap] = x;
+        float rof = cRof[w];
+        if (full) {
+          float sw, aw;
+          if (j < kWin && !refresh) {
+            win_s[j] += x;
+            win_a[j] += fabsf(x);
+            sw = win_s[j];
+            aw = win_a[j];
+          } else {
+            window_sums(hw, sw, aw);
+            if (j < kWin) {
+              win_s[j] = sw;
+              win_a[j] = aw;
+            }
+          }
+          rof = next_rof(hw, sw, aw, rof);
+        } else {
+          rof = fminf(rof * r_fac, 1.0f);
+        }
+        cRof[w] = rof;
+      }
+    } else {
+      for (int w = l; w < Rrev; w += G) {
+        float* hw = cHist + w * NP;
+        const float x = hw[ktap] * hf;
+        hw[ktap] = x;
+        float rof = cRof[w];
+        if (full) {
+          float sw, aw;
+          window_sums(hw, sw, aw);
+          rof = next_rof(hw, sw, aw, rof);
+        } else {
+          rof = fminf(rof * r_fac, 1.0f);
+        }
+        cRof[w] = rof;
+      }
     }
     st.nhist += 1;
   }
@@ -629,6 +736,11 @@ __device__ __forceinline__ void mixed_kernel_body(const Launch& L, unsigned char
   const int warp = threadIdx.x >> 5;
   float* net_q0 = mixed_cell(L, smem_raw + tables + (size_t)(warp * (32 / G)) * cell_bytes, MLP).Q;
   const int cell_ld = (int)(cell_bytes / sizeof(float));
+  // the damper's running window sums (WinRegs; unused elsewhere)
+  constexpr int kWin = WinRegs<G, NT, MLP>::n;
+  float win_s[kWin > 0 ? kWin : 1], win_a[kWin > 0 ? kWin : 1];
+#pragma unroll
+  for (int j = 0; j < (kWin > 0 ? kWin : 1); ++j) win_s[j] = win_a[j] = 0.0f;
 
   const unsigned long long n = (unsigned long long)L.n_cells;
   CellState st = idle_cell_state();
@@ -665,7 +777,8 @@ __device__ __forceinline__ void mixed_kernel_body(const Launch& L, unsigned char
     idle_since = 0;
     idle_sleep = 1000u;
     const int outcome = step_mixed<G, MLP, NT>(L, tb, cs.Yh, cs.Yl, cs.G2, cs.C, cs.H, cs.Q,
-                                               cs.Hist, cs.Rof, Pf, l, st, net_q0, cell_ld);
+                                               cs.Hist, cs.Rof, Pf, l, st, net_q0, cell_ld,
+                                               win_s, win_a);
     if (st.cell >= 0 && outcome >= 0) store_mixed_cell<G>(L, l, cs, st, outcome);
   }
 }

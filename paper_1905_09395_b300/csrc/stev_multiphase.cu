@@ -46,9 +46,10 @@ constexpr int kMaxN = 32;  // DFT window (options.dft_n <= 32)
 enum { iO2, iCO, iCO2, iCH4, iH2, iH2O, iH2S, iC3H6, iHCN, iC2H4, iC2H6, iTAR, iSO3, iN2,
        iCV, iCC, iCM, iCA };
 
-// molecular weights (kg/kmol), set by the host (mp_weights)
+// molecular weights (kg/kmol) and their reciprocals, set by the host
 struct Weights {
   double w[kNSp];
+  double inv[kNSp];
 };
 
 struct Params {
@@ -95,6 +96,10 @@ __device__ __forceinline__ double gam(double x, double alpha) {
   return alpha > 0.0 ? y / (alpha + y) : (y > 0.0 ? 1.0 : 0.0);
 }
 __device__ __forceinline__ double ppow(double x, double a) { return pow(fmax(x, 0.0), a); }
+// the rate laws' half-integer and quarter powers by square roots (a pow costs
+// an exp and a log on the FP64 pipe)
+__device__ __forceinline__ double psqrt(double x) { return sqrt(fmax(x, 0.0)); }
+__device__ __forceinline__ double pqrt(double x) { return sqrt(sqrt(fmax(x, 0.0))); }
 
 // Per-cell constants: the Arrhenius factors at the held temperatures, the WGS
 // pressure factor.
@@ -106,7 +111,6 @@ struct CellConst {
 // Eqs. 42-56 at partial densities c: raw rates of progress r[11].
 __device__ __forceinline__ void rates(const Params& L, const CellConst& k, const double* c,
                                       double* X, double* r) {
-  const double* w = L.mw.w;
   double mg = 0.0, ms = 0.0;
 #pragma unroll
   for (int i = 0; i < kNG; ++i) mg += c[i];
@@ -117,7 +121,7 @@ __device__ __forceinline__ void rates(const Params& L, const CellConst& k, const
 #pragma unroll
   for (int i = 0; i < kNG; ++i) {
     X[i] = c[i] * img;
-    inv_mw += X[i] / w[i];
+    inv_mw = fma(X[i], L.mw.inv[i], inv_mw);
   }
 #pragma unroll
   for (int i = kNG; i < kNSp; ++i) X[i] = c[i] * ims;
@@ -142,13 +146,15 @@ __device__ __forceinline__ void rates(const Params& L, const CellConst& k, const
   r[4] = k.kmeg * aG * solid_cc * (pw * X[iH2] / 2.01588);                              // Eq. 49
   r[5] = aC * k.kcox * gam(X[iO2], al) * gam(X[iCC], al) *                              // Eq. 50
          ppow(pw * X[iO2] / 31.9988, 0.73) * es / k.dp;
-  const double rg175 = pow(rg, 1.75);
-  r[6] = k.ktox * eg * rg175 * ppow(X[iO2], 1.5) * ppow(X[iTAR], 0.25) *                 // Eq. 52
+  const double rg_h = sqrt(rg), rg_q = sqrt(rg_h);
+  const double rg175 = rg * rg_h * rg_q, rg15 = rg * rg_h;
+  const double o2_q = pqrt(X[iO2]), o2_h = psqrt(X[iO2]);
+  r[6] = k.ktox * eg * rg175 * (fmax(X[iO2], 0.0) * o2_h) * pqrt(X[iTAR]) *              // Eq. 52
          gam(X[iO2], al) * gam(X[iTAR], al);
-  r[7] = k.kcoox * eg * rg175 * ppow(X[iO2], 0.25) * X[iCO] * ppow(X[iH2O], 0.5) *       // Eq. 53
+  r[7] = k.kcoox * eg * rg175 * o2_q * X[iCO] * psqrt(X[iH2O]) *                         // Eq. 53
          gam(X[iO2], al) * gam(X[iCO], al);
   r[8] = k.khox * eg * rg * rg * X[iO2] * X[iH2] * gam(X[iO2], al) * gam(X[iH2], al);   // Eq. 54
-  r[9] = k.kmeox * eg * pow(rg, 1.5) * ppow(X[iO2], 1.3) * ppow(X[iCH4], 0.2) *          // Eq. 55
+  r[9] = k.kmeox * eg * rg15 * ppow(X[iO2], 1.3) * ppow(X[iCH4], 0.2) *                  // Eq. 55
          gam(X[iO2], al) * gam(X[iCH4], al);
   r[10] = kAmr * gam(X[iCM], al) * es / k.dp;                                            // Eq. 56
 }
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) stev_mp_kernel(const Params L) {
   double c[kNSp];
   double inv_mw = 0.0;
 #pragma unroll
-  for (int i = 0; i < kNG; ++i) inv_mw += in[i] / w[i];
+  for (int i = 0; i < kNG; ++i) inv_mw += in[i] / w[i];  // once per cell
   const double rg0 = k.P / (inv_mw * kRu * Tg);
   const double es0 = in[20];
 #pragma unroll
@@ -236,10 +242,11 @@ __global__ void __launch_bounds__(kThreads) stev_mp_kernel(const Params L) {
     for (int i = kNG; i < kNSp; ++i) ms += c[i];
     // Eqs. 1-5 on the phase mass fractions
     double tstar = INFINITY;
+    const double img = 1.0 / mg, ims = 1.0 / ms;
 #pragma unroll
     for (int i = 0; i < kNSp; ++i) {
-      const double M = i < kNG ? mg : ms, dM = i < kNG ? dmg : dms;
-      const double dX = (wd[i] - (c[i] / M) * dM) / M;
+      const double iM = i < kNG ? img : ims, dM = i < kNG ? dmg : dms;
+      const double dX = (wd[i] - X[i] * dM) * iM;
       const double rstar = fmax(-dX, 1.0e-30);
       const double ystar = (X[i] < 1.0e-20) ? 1.0 : 0.9 * X[i];
       tstar = fmin(tstar, fmin(L.y_step_max, ystar) / rstar);
@@ -333,6 +340,7 @@ static Weights weights() {
            0.198778 * w[iH2O] + 0.0112077 * w[iH2S] + 0.024509 * w[iC3H6] +
            0.0266777 * w[iHCN] + 0.0473162 * w[iC2H4] + 0.008257 * w[iC2H6] +
            0.02146 * w[iTAR];
+  for (int i = 0; i < kNSp; ++i) m.inv[i] = 1.0 / w[i];
   return m;
 }
 

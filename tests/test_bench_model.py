@@ -44,3 +44,12 @@ def test_roofline_fraction_reproduces_the_measured_round_numbers():
     n = bench.alu_roofline("mixed", 32, 150, True, 3.52e8, 1.0, 2032.0)
     assert n["frac"] == pytest.approx(0.05, abs=0.003)
     assert n["cell_steps_per_s_bound"] * n["frac"] == pytest.approx(3.52e8)
+
+
+def test_multiphase_bound_by_hand():
+    """The multiphase cell-step: 420 flops on the FP64 pipe, 112 divisions and
+    11 powers (exp + log) at CUDA's double rates."""
+    clk = 148 * 2032e6
+    t = 420 / (2 * 1.668 * clk) + 112 / (0.222 * clk) + 11 * (1 / (0.104 * clk) + 1 / (0.055 * clk))
+    assert bench.mp_bound_s_per_cell_step(2032.0) == pytest.approx(t)
+    assert 1.0 / t == pytest.approx(3.2e8, rel=0.03)
