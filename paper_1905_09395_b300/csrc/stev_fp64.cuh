@@ -160,15 +160,22 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
             // D0 < Tol_ring max|X_j|, compared as squares in units of sum|x_m|
             // (every scaled magnitude is <= 1, so the squares cannot underflow)
             const double inv = 1.0 / a;
+            // taps m and N - m paired: cos is even and sin odd in m about
+            // N / 2 (tw[b] = cos, sin of -2 pi j m / N), so Re X_j = x_0 +
+            // sum (x_m + x_{N-m}) cos_m (+ an even N's middle tap) and Im X_j
+            // = sum (x_m - x_{N-m}) sin_m, m = 1 .. (N - 1) / 2
             double max2 = 0.0;
+            const double* xw = cHist + w;
+            const int half = (N - 1) / 2;
             for (int bb = 0; bb < L.n_hi_bins; ++bb) {
               const double* c = tb.tw + bb * 2 * N;
-              double re = 0.0, im = 0.0;
-              for (int m = 0; m < N; ++m) {
-                const double xm = cHist[m * Rrev + w];
-                re = fma(xm, c[m], re);
-                im = fma(xm, c[N + m], im);
+              double re = xw[0], im = 0.0;
+              for (int m = 1; m <= half; ++m) {
+                const double xa = xw[m * Rrev], xb = xw[(N - m) * Rrev];
+                re = fma(xa + xb, c[m], re);
+                im = fma(xa - xb, c[N + m], im);
               }
+              if (!(N & 1)) re = fma(xw[(N / 2) * Rrev], c[N / 2], re);
               re *= inv;
               im *= inv;
               max2 = fmax(max2, fma(re, re, im * im));

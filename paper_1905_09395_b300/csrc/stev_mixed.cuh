@@ -181,8 +181,10 @@ struct TablesF {
   const float* gnu;   // general rate laws: [n_gather] nu
 };
 
-// Adds nu * (g.x + g.y) to the float pair (s, e) (s + e = the exact sum so
-// far to ~2^-48): the product's rounding error by fma, the sum's by TwoSum.
+// Adds nu * (g.x + g.y) to the sum s + e of a general reaction's exponent
+// (g = (k, f) of gibbs_split): nu k and its rounding error by fma into s by
+// TwoSum, nu f and the errors into e, so that s + e is exact but for the
+// roundings of e (terms below a few units: ~2^-22 absolute).
 __device__ __forceinline__ void pair_add_scaled(float nu, float2 g, float& s, float& e) {
   const float p = nu * g.x;
   const float pe = fmaf(nu, g.x, -p);
@@ -210,21 +212,84 @@ __device__ __forceinline__ float lg2f_approx(float x) {
 }
 
 // The reverse term kr C_p0 C_p1 of an elementary reaction (Eqs. 29-30):
-// kr = kf 2^x with x = sum nu g2 as a float pair (s, e), TwoSum on the high
-// parts and plain sums of the error terms and low parts, so that the
-// exponent keeps no cancellation loss before its single rounding.
+// kr = kf 2^x with x = sum nu g2.  Each species' g2 is held as (k, f), k the
+// integer nearest to it and f the rest (gibbs_split), so that the integer
+// parts of the sum cancel exactly and only the fractions (|f| <= 1/2) are
+// rounded: x before its one rounding is exact to a few 2^-25.
 __device__ __forceinline__ float reverse_term(const float2* cG2, const float* cC, int a0, int a1,
                                               int p0, int p1, float lg2kf) {
   const float2 gp0 = cG2[p0], ga0 = cG2[a0], ga1 = cG2[a1], gp1 = cG2[p1];
-  float sx, e, t;
-  two_sum(gp0.x, -ga0.x, sx, t);
-  e = t + (gp0.y - ga0.y);
-  two_sum(sx, -ga1.x, sx, t);
-  e += t - ga1.y;
-  two_sum(sx, gp1.x, sx, t);
-  e += t + gp1.y;
-  const float x = sx + e;
-  return ex2f(lg2kf + x) * cC[p0] * cC[p1];
+  const float kx = (gp0.x - ga0.x) + (gp1.x - ga1.x);  // integers below 2^24: exact
+  const float fx = (gp0.y - ga0.y) + (gp1.y - ga1.y);
+  return ex2f(lg2kf + (kx + fx)) * cC[p0] * cC[p1];
+}
+
+// g2 = h + l (a float pair) as (k, f): k = rint(h), f = (h - k) + l, where
+// h - k is exact (the fractional bits of h), so k + f = g2 to one rounding of
+// a number below 1 in magnitude.
+__device__ __forceinline__ float2 gibbs_split(FF g2) {
+  const float k = rintf(g2.h);
+  return make_float2(k, (g2.h - k) + g2.l);
+}
+
+// The stoichiometric coefficient of an elementary gather entry (gather_pack:
+// reaction * 16 + nu + 8): nu = code - 8, formed as (2^23 + code) - (2^23 + 8)
+// from the float bits, exact.
+__device__ __forceinline__ float nu_of_code(int e) {
+  return __int_as_float(0x4B000000 | (e & 15)) - 8388616.0f;
+}
+
+// Eq. 10's largest high-frequency |X_j|^2 (bins j = hi_first ...) of a full
+// window hw[N] in storage order (|X_j| does not depend on the rotation),
+// scaled by inv^2.  The twiddle rows of bin b are tw[b][0..N) = cos(-2 pi j
+// k / N) and tw[b][N..2N) = sin(-2 pi j k / N); since cos(theta_{N-k}) =
+// cos(theta_k) and sin(theta_{N-k}) = -sin(theta_k), taps k and N - k are
+// paired: Re X_j = x_0 + sum_k (x_k + x_{N-k}) cos_k (+ the middle tap of an
+// even N), Im X_j = sum_k (x_k - x_{N-k}) sin_k, k = 1 .. (N - 1) / 2.
+template <int NT>
+__device__ __forceinline__ float hi_bins_max2(const float* hw, int N, const float* tw, int n_bins,
+                                              float inv) {
+  float max2 = 0.0f;
+  if constexpr (NT > 0 && (NT & 1)) {
+    constexpr int kHalf = (NT - 1) / 2;
+    float u[kHalf], v[kHalf];
+#pragma unroll
+    for (int k = 1; k <= kHalf; ++k) {
+      const float a = hw[k], b = hw[NT - k];
+      u[k - 1] = a + b;
+      v[k - 1] = a - b;
+    }
+    const float x0 = hw[0];
+#pragma unroll 1
+    for (int bb = 0; bb < n_bins; ++bb) {
+      const float* c = tw + bb * 2 * NT;
+      float re = x0, im = 0.0f;
+#pragma unroll
+      for (int k = 1; k <= kHalf; ++k) {
+        re = fmaf(u[k - 1], c[k], re);
+        im = fmaf(v[k - 1], c[NT + k], im);
+      }
+      re *= inv;
+      im *= inv;
+      max2 = fmaxf(max2, fmaf(re, re, im * im));
+    }
+  } else {
+    const int half = (N - 1) / 2;
+    for (int bb = 0; bb < n_bins; ++bb) {
+      const float* c = tw + bb * 2 * N;
+      float re = hw[0], im = 0.0f;
+      for (int k = 1; k <= half; ++k) {
+        const float a = hw[k], b = hw[N - k];
+        re = fmaf(a + b, c[k], re);
+        im = fmaf(a - b, c[N + k], im);
+      }
+      if (!(N & 1)) re = fmaf(hw[N / 2], c[N / 2], re);
+      re *= inv;
+      im *= inv;
+      max2 = fmaxf(max2, fmaf(re, re, im * im));
+    }
+  }
+  return max2;
 }
 
 // MLP = true: cp/R (and, with L.mlp_h, H/RT) come from the thermo network
@@ -308,8 +373,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     dot2_term(g[8 * S], g[9 * S], T2, gs, ge);
     dot2_term(g[10 * S], g[11 * S], T3, gs, ge);
     dot2_term(g[12 * S], g[13 * S], T4, gs, ge);
-    const FF g2 = ff_norm(gs, ge);
-    cG2[i] = make_float2(g2.h, g2.l);
+    cG2[i] = gibbs_split(ff_norm(gs, ge));
     const float y = fmaxf(Yi, 0.0f);
     const float ys = (L.alpha_f > 0.0f) ? y * __fdividef(y, L.alpha_f + y) : y;
     cC[i] = rho * ys * f[SF_INVW * S];
@@ -403,7 +467,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
     float wd = 0.0f;
     for (int k = tb.gptr[i]; k < tb.gptr[i + 1]; ++k) {
       const int e = tb.gent[k];
-      wd = fmaf(mGeneral(L) ? tb.gnu[k] : kNuOfF[e & 15], cQ[e >> 4], wd);
+      wd = fmaf(mGeneral(L) ? tb.gnu[k] : nu_of_code(e), cQ[e >> 4], wd);
     }
     const float ri = tb.spf[SF_W * S + i] * wd * invRho;
     hwp = fmaf(cH[i], wd, hwp);
@@ -444,20 +508,7 @@ __device__ __forceinline__ int step_mixed(const Launch& L, const TablesF& tb, fl
       float rstar = r_fac;
       if (D0 < tol_freq && D0 < tol_ring * a) {
         const float inv = 1.0f / a;
-        float max2 = 0.0f;
-        for (int bb = 0; bb < L.n_hi_bins; ++bb) {
-          const float* c = tb.tw + bb * 2 * N;
-          float re = 0.0f, im = 0.0f;
-#pragma unroll 1
-          for (int m = 0; m < N; ++m) {  // rare: not unrolled, taps reloaded
-            const float xm = hw[m];
-            re = fmaf(xm, c[m], re);
-            im = fmaf(xm, c[N + m], im);
-          }
-          re *= inv;
-          im *= inv;
-          max2 = fmaxf(max2, fmaf(re, re, im * im));
-        }
+        const float max2 = hi_bins_max2<NT>(hw, N, tb.tw, L.n_hi_bins, inv);
         const float d = D0 * inv;
         if (d * d < tol_ring * tol_ring * max2) rstar = L.inv_r_fac_f;
       }
