@@ -55,11 +55,11 @@ enum { SF_W = 0, SF_INVW = 1, SF_SPLIT_H = 2, SF_SPLIT_L = 3, SF_LOW = 4, SF_HIG
 enum { BF_A0 = 0, BF_A1, BF_A2, BF_A3, BF_A4, BF_A5, BF_H1, BF_H2, BF_H3, BF_H4, BF_SIZE };
 enum { GF_SIZE = 14 };  // rows of one range's Gibbs block: c_k hi at 2k, lo at 2k + 1
 
-// gather entry: reaction index * 16 + (nu + 8); the stoichiometric factor is
-// read back from kNuOf[] so that no integer-to-double conversion is needed
+// gather entry: reaction index * 16 + (nu + 8); the FP64 kernel reads the
+// stoichiometric factor back from kNuOf[] (no integer-to-double conversion),
+// the mixed kernels form it from the entry's bits (nu_of_code)
 __host__ __device__ inline int gather_pack(int r, int nu) { return r * 16 + (nu + 8); }
 __constant__ double kNuOf[16] = {0, 0, 0, 0, 0, 0, -2.0, -1.0, 0, 1.0, 2.0, 0, 0, 0, 0, 0};
-__constant__ float kNuOfF[16] = {0, 0, 0, 0, 0, 0, -2.0f, -1.0f, 0, 1.0f, 2.0f, 0, 0, 0, 0, 0};
 
 // The network's weights in MMA fragment order for inference inside the solver
 // (the weights are the A operand of m16n8k16, 16 output units per tile; the
