@@ -303,10 +303,12 @@ stev_status stev_mlp_jacobian(stev_mechanism *mech, const float *params, const d
  * used): n x n, full (both triangles), row stride ldg >= n.  The products are
  * taken on the tensor cores in TF32 (inputs rounded to 10-bit mantissas, as
  * the hardware's TF32 mode does) and accumulated in FP32 (the Gauss-Newton
- * matrix of the trainer; a 128 x 128 tile per CTA, operands staged by TMA).
- * X must be 16-byte aligned, ldx >= k a multiple of 4.  STEV_EINVAL on bad
- * sizes; STEV_ETIMEOUT if a wait of the kernel's pipeline ran out (never
- * expected; the kernel then stops and G is incomplete). */
+ * matrix of the trainer; a 128 x 256 tile per CTA, operands staged by TMA).
+ * X must be 16-byte aligned, ldx >= k a multiple of 4.  The call is
+ * synchronous (it reads back the kernel's error flag, allocated from the
+ * stream's memory pool).  STEV_EINVAL on bad sizes; STEV_ETIMEOUT if a wait of
+ * the kernel's pipeline ran out (never expected; the kernel then stops and G
+ * is incomplete). */
 stev_status stev_gram_tf32(long n, long k, const float *X, long ldx, float *G, long ldg,
                            void *cuda_stream);
 

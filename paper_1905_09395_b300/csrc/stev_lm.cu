@@ -10,15 +10,20 @@
 //               the Jacobi preconditioner, the matrix-vector product one warp
 //               per row of A, dot products reduced in a fixed order.
 //
-// Gram kernel layout.  One CTA of 4 warps per 128 x 128 tile of the lower
-// triangle of G (tile row ti >= tile column tj).  The K dimension (the rows of
-// J) runs in blocks of 32 FP32 values (128 bytes, the 128-byte swizzle of the
-// TMA and of the MMA's shared-memory descriptors) through a 4-stage ring:
-// warp 0 issues the TMA loads, warp 1 the MMAs (one thread each; 4 MMAs of
-// K = 8 per block), and all four warps read the 128 x 128 FP32 accumulator
-// back from tensor memory (warp w: lanes 32w .. 32w + 31) and store it twice,
-// as the tile and as its mirror, so G is full.  Every wait is bounded by time;
-// on a timeout the kernel records it in *err, waits (bounded) for the loads it
+// Gram kernel layout.  One CTA of 4 warps per 128 x 256 tile of G (rows ti,
+// columns tj; the column blocks of a row block run up to its diagonal).  The
+// K dimension (the rows of J) runs in blocks of 32 FP32 values (128 bytes, the
+// 128-byte swizzle of the TMA and of the MMA's shared-memory descriptors)
+// through a 4-stage ring of 48 KB (A: 128 rows, B: 256 rows in two TMA
+// boxes): warp 0 issues the TMA loads, warp 1 the MMAs (one thread each;
+// 4 MMAs of M = 128, N = 256, K = 8 per block), and all four warps read the
+// 128 x 256 FP32 accumulator back from tensor memory (warp w: lanes 32w ..
+// 32w + 31) and store every element on or below the diagonal twice, as
+// G[r][c] and G[c][r], so G is full and exactly symmetric.  A 256-column B
+// tile reads each A row block half as often as square 128 x 128 tiles do
+// (measured at 10,624 x 49,152: 10.4 ms against 11.5 ms with square tiles
+// and six stages, 14.1 ms with four).  Every wait is bounded by time; on a
+// timeout the kernel records it in *err, waits (bounded) for the loads it
 // issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -32,14 +37,16 @@
 namespace stev {
 namespace lm {
 
-constexpr int kTile = 128;          // M = N of the MMA, rows of a tile
+constexpr int kTile = 128;          // M of the MMA: rows of a tile (the A operand)
+constexpr int kTileN = 256;         // N of the MMA: columns of a tile (the B operand)
 constexpr int kKBlock = 32;         // FP32 values per 128-byte row of a stage
 constexpr int kStages = 4;
-constexpr int kStageBytes = kTile * kKBlock * 4;   // 16 KB per operand
+constexpr int kStageBytes = kTile * kKBlock * 4;   // 16 KB: A, and each half of B
+constexpr int kStageBytesB = kTileN * kKBlock * 4; // 32 KB
 constexpr int kGramThreads = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 // dynamic shared memory: 1024-byte alignment slack, A and B rings, barriers
-constexpr size_t kGramSmem = 1024 + 2 * kStages * kStageBytes + 256;
+constexpr size_t kGramSmem = 1024 + kStages * (kStageBytes + kStageBytesB) + 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -90,7 +97,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 }
 // Instruction descriptor of kind::tf32: D in FP32, A and B TF32, both
 // K-major, N = M = 128.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) |
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
                                 ((uint32_t)(kTile >> 4) << 24);
 
 __device__ __forceinline__ void umma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
@@ -129,13 +136,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Tile (ti, tj), ti >= tj, of the lower triangle from the linear tile index.
+// Tiles before row block ti: row block t (128 rows) holds the column blocks
+// tj = 0 .. t / 2 (256 columns) that reach the diagonal, so C(2m) = m (m + 1)
+// and C(2m + 1) = (m + 1)^2.
+__host__ __device__ __forceinline__ long long tiles_before(long long ti) {
+  const long long m = ti / 2;
+  return (ti & 1) ? (m + 1) * (m + 1) : m * (m + 1);
+}
+// Tile (ti, tj) of the lower triangle from the linear tile index.
 __device__ __forceinline__ void tile_of(int t, int& ti, int& tj) {
-  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((i + 1) * (i + 2) / 2 <= t) ++i;
-  while (i * (i + 1) / 2 > t) --i;
+  int i = (int)(2.0 * sqrt((double)t));
+  while (i > 0 && tiles_before(i) > t) --i;
+  while (tiles_before(i + 1) <= t) ++i;
   ti = i;
-  tj = t - i * (i + 1) / 2;
+  tj = (int)(t - tiles_before(i));
 }
 
 __global__ void __launch_bounds__(kGramThreads, 1)
@@ -145,8 +159,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sa = base;                                  // [kStages][128][32] FP32
-  unsigned char* sb = base + kStages * kStageBytes;          // [kStages][128][32] FP32
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * kStages * kStageBytes);
+  unsigned char* sb = base + kStages * kStageBytes;          // [kStages][256][32] FP32
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kStages * kStageBytesB);
   // bars[0 .. S-1] full, [S .. 2S-1] empty, [2S] done; the TMEM address after
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
   __shared__ int s_fail;
@@ -164,7 +178,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(kTile)
+                 "r"(kTileN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -183,9 +197,11 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       }
       if (*(volatile int*)&s_fail) break;
       const uint32_t full = smem_u32(bars + s);
-      mbar_expect_tx(full, 2 * kStageBytes);
+      mbar_expect_tx(full, kStageBytes + kStageBytesB);
       tma_load_2d(smem_u32(sa + s * kStageBytes), &xmap, kb * kKBlock, ti * kTile, full);
-      tma_load_2d(smem_u32(sb + s * kStageBytes), &xmap, kb * kKBlock, tj * kTile, full);
+      tma_load_2d(smem_u32(sb + s * kStageBytesB), &xmap, kb * kKBlock, tj * kTileN, full);
+      tma_load_2d(smem_u32(sb + s * kStageBytesB + kStageBytes), &xmap, kb * kKBlock,
+                  tj * kTileN + kTile, full);
       issued = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -196,7 +212,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sa + s * kStageBytes), b0 = smem_u32(sb + s * kStageBytes);
+      const uint32_t a0 = smem_u32(sa + s * kStageBytes), b0 = smem_u32(sb + s * kStageBytesB);
 #pragma unroll
       for (int kk = 0; kk < kKBlock / 8; ++kk)
         umma_tf32(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0);
@@ -210,20 +226,20 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   tc_fence_after();
   if (done && !*(volatile int*)&s_fail) {
     const int r = ti * kTile + warp * 32 + lane;
-    for (int c0 = 0; c0 < kTile; c0 += 32) {
+    const int cmax = min(r, n - 1);  // G[r][c] for c <= r, and its mirror
+    for (int c0 = 0; c0 < kTileN; c0 += 32) {
+      const int cb = tj * kTileN + c0;
+      if (cb > ti * kTile + kTile - 1) break;  // warp-uniform: past every row's diagonal
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      const int cb = tj * kTile + c0;
-      // mirror (coalesced: consecutive lanes, consecutive rows of G^T)
       if (r < n) {
+        // mirror (coalesced: consecutive lanes, consecutive rows of G^T)
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (cb + j < n) G[(long long)(cb + j) * ldg + r] = v[j];
-      }
-      if (ti != tj && r < n) {
+          if (cb + j <= cmax) G[(long long)(cb + j) * ldg + r] = v[j];
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (cb + j < n) G[(long long)r * ldg + cb + j] = v[j];
+          if (cb + j < cmax) G[(long long)r * ldg + cb + j] = v[j];
       }
     }
   } else if (threadIdx.x == 0) {
@@ -239,7 +255,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN)
                  : "memory");
   }
 }
@@ -399,7 +415,7 @@ stev_status gram_tf32(const float* X, long long n, long long k, long long ldx, f
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(STEV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
   const long long nt = (n + lm::kTile - 1) / lm::kTile;
-  const long long tiles = nt * (nt + 1) / 2;
+  const long long tiles = lm::tiles_before(nt);
   cudaError_t e = cudaFuncSetAttribute(lm::gram_tf32_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm::kGramSmem);
   if (e != cudaSuccess) return fail(STEV_ECUDA, "gram: %s", cudaGetErrorString(e));
@@ -493,9 +509,12 @@ extern "C" stev_status stev_gram_tf32(long n, long k, const float* X, long ldx, 
                                       void* stream) {
   stev::host::clear_error();
   if (!X || !G) return stev::host::fail(STEV_EINVAL, "NULL array");
-  int* d_err = dev_alloc<int>(1);
-  if (!d_err) return stev::host::fail(STEV_ENOMEM, "cudaMalloc failed");
+  // the error flag from the stream's memory pool: no device-wide
+  // synchronisation, unlike cudaMalloc / cudaFree
   cudaStream_t s = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d_err), sizeof(int), s) != cudaSuccess || !d_err)
+    return stev::host::fail(STEV_ENOMEM, "cudaMallocAsync failed");
   stev_status st = STEV_OK;
   if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess)
     st = stev::host::fail(STEV_ECUDA, "cudaMemsetAsync failed");
@@ -505,7 +524,7 @@ extern "C" stev_status stev_gram_tf32(long n, long k, const float* X, long ldx, 
                         cudaStreamSynchronize(s) != cudaSuccess))
     st = stev::host::fail(STEV_ECUDA, "gram: %s", cudaGetErrorString(cudaGetLastError()));
   if (st == STEV_OK && h_err) st = stev::host::fail(STEV_ETIMEOUT, "gram: a pipeline wait timed out");
-  cudaFree(d_err);
+  cudaFreeAsync(d_err, s);
   return st;
 }
 
