@@ -4,7 +4,8 @@ stoichiometry (1.5 O2, 0.5 O2), through stev_mechanism_create_orders.
 
 Same parity methodology as test_gpu_fp64 / test_gpu_mixed: prefix parity
 step by step, then full solves on the cells the oracle's conditioning probe
-marks well-conditioned, validity bounds elsewhere."""
+marks well-conditioned, a bound by the probes' spread elsewhere, and the
+deviations distributed like one probe run's."""
 import numpy as np
 import pytest
 
@@ -48,9 +49,10 @@ def test_bfer_full_solve_fp64():
     # Scaling kf or K moves that fixed point without making it inexact, so the
     # probes cannot see this sensitivity.
     mech, T, P, Y = _case()
-    base, sY, sT = oracle.conditioning(mech, T, P, Y, 1e-3)
+    runs = {}
+    base, sY, sT = oracle.conditioning(mech, T, P, Y, 1e-3, per_run=runs)
     gpu = _gpu_solve(mech, T, P, Y, 1e-3)
-    r = _full(gpu, base, sY, sT, mech, T, Y, min_well=0.3, outliers=0.002)
+    r = _full(gpu, base, sY, sT, mech, T, Y, min_well=0.3, outliers=0.002, runs=runs)
     print("BFER FP64 x %d:" % len(T), {k: float("%.4g" % v) for k, v in r.items()})
     assert (gpu[3] == 0).all()
     assert gpu[0].mean() > T.mean() + 100.0          # the methane burns
@@ -58,7 +60,8 @@ def test_bfer_full_solve_fp64():
 
 def test_bfer_full_solve_mixed():
     mech, T, P, Y = _case()
-    base, sY, sT = oracle.conditioning(mech, T, P, Y, 1e-3, level="fp32")
+    runs = {}
+    base, sY, sT = oracle.conditioning(mech, T, P, Y, 1e-3, level="fp32", per_run=runs)
     m = Mechanism(mech, precision=MIXED)
     import torch
     d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (T, P, Y)]
@@ -66,7 +69,7 @@ def test_bfer_full_solve_mixed():
     # at most 1% of the FP32-conditioned cells past the target (the exact
     # equilibrium cancellation of test_bfer_full_solve_fp64 again), capped
     within = _check(mech, T, Y, gpu, base, sY, sT, "BFER mixed x %d" % len(T),
-                    outliers=0.01, outlier_cap=(5e-4, 0.5))
+                    outliers=0.01, outlier_cap=(5e-4, 0.5), runs=runs)
     # only ~12% of BFER cells are well-conditioned at FP32 rounding (the steep
     # 0.5-order rate near CH4 depletion, COROX at equilibrium): the target
     # holds on those, about half of all cells meet it, the rest stay within

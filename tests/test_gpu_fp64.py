@@ -13,11 +13,15 @@ workload's cells by more than 1e-8, up to 2.4e-4).  So parity is checked as:
 2. full-solve parity at 1e-8 / 1e-6 K on every cell the oracle's own
    conditioning probe shows to be well-conditioned (spread < 1e-10);
 3. on the remaining cells, the GPU lies within the spread the oracle itself
-   shows under rounding-size rate changes (times a margin) or within twice
-   the limiter's per-step bound Y_step^max (a ringing phase moved), its T
-   within the two trajectories' first-order enthalpy drift (forward Euler
-   does not conserve H exactly), and it conserves mass and elements;
-4. identical per-cell status everywhere.
+   shows under rounding-size rate changes (times a margin: the GPU's rates
+   differ from the oracle's by tens of ulp, not the probes' one), its T
+   within that plus the two trajectories' first-order enthalpy drift (forward
+   Euler does not conserve H exactly), and it conserves mass and elements;
+4. the GPU's deviations over the ill-conditioned cells are distributed like
+   one probe run's: their median, 90th and 99th percentiles within a small
+   factor of the largest single probe's (a dropped term or a wrong sign moves
+   every cell, and these statistics with them, by far more);
+5. identical per-cell status everywhere.
 """
 import numpy as np
 import pytest
@@ -31,6 +35,7 @@ TOL_Y, TOL_T = 1e-8, 1e-6          # the full-solve bar
 PREFIX_Y, PREFIX_T = 1e-10, 1e-7   # before divergence can build up
 WELL_Y, WELL_T = 1e-10, 1e-8       # oracle probe spread of a well-conditioned cell
 SPREAD_MARGIN = 1e3                # 3: |gpu - oracle| <= margin * spread + bar
+DISTRIB = 4.0                      # 4: median / p90 / p99 bound, multiples of a probe's
 
 
 def _dev(*arrays):
@@ -71,11 +76,27 @@ def _enthalpy(mech, T, Y):
     return H, cp, hW
 
 
+def _distribution(dev, probes, ill, label, factor=DISTRIB):
+    """The GPU's deviations over the ill-conditioned cells against each probe
+    run's own deviations there (item 4)."""
+    if ill.sum() < 20:
+        return
+    for q in (50, 90, 99):
+        got = np.percentile(dev[ill], q)
+        ref = max(np.percentile(p[ill], q) for p in probes)
+        print("%s p%d: %.3g (largest probe's %.3g)" % (label, q, got, ref))
+        assert got <= factor * ref, "%s: p%d %.3g over %g x the probes' %.3g" % (
+            label, q, got, factor, ref)
+
+
 def _full(gpu, ref, spread_Y, spread_T, mech=None, T0=None, Y0=None, y_step_max=1e-3,
-          min_well=0.3, outliers=0.0):
-    """Full-solve parity (module docstring, items 2-4).  outliers: fraction of
-    probe-well-conditioned cells allowed past the bar (still held to the
-    validity bounds), for sensitivities the rate-scaling probes cannot reach."""
+          min_well=0.3, outliers=0.0, runs=None):
+    """Full-solve parity (module docstring, items 2-5).  outliers: fraction of
+    probe-well-conditioned cells allowed past the bar, each still within
+    twice the limiter's per-step bound Y_step^max, for a sensitivity the
+    rate-scaling probes cannot reach (an equilibrium that cancels exactly in
+    the oracle's arithmetic, test_gpu_bfer).  runs: the probe runs' own
+    per-cell deviations (oracle.conditioning's per_run) for item 4."""
     To, Yo, it, st = gpu
     rT, rY, rit, rst = ref
     assert (st == rst).all(), "status differs in %d cells" % int((st != rst).sum())
@@ -86,11 +107,13 @@ def _full(gpu, ref, spread_Y, spread_T, mech=None, T0=None, Y0=None, y_step_max=
     bad = np.nonzero(well & ((dY > TOL_Y) | (dT > TOL_T)))[0]
     assert bad.size <= outliers * well.sum(), "well-conditioned cells over the bar: %s dY %s dT %s" % (
         bad[:8], dY[bad[:8]], dT[bad[:8]])
-    # the rest: Y within the oracle's own spread, or within the limiter's
-    # per-step bound twice over (a ringing phase moved by rounding)
-    limY = np.maximum(TOL_Y + SPREAD_MARGIN * spread_Y, 2.0 * y_step_max)
+    assert np.all(dY[bad] <= 2.0 * y_step_max), "outliers beyond 2 Y_step^max: %s" % dY[bad]
+    # the rest: Y within the oracle's own spread times the margin
+    limY = TOL_Y + SPREAD_MARGIN * spread_Y
+    limY[bad] = 2.0 * y_step_max
     over = np.nonzero(dY > limY)[0]
-    assert over.size == 0, "cells beyond the Y bound: %s dY %s" % (over[:8], dY[over[:8]])
+    assert over.size == 0, "cells beyond the Y bound: %s dY %s spread %s" % (
+        over[:8], dY[over[:8]], spread_Y[over[:8]])
     limT = TOL_T + SPREAD_MARGIN * spread_T
     if mech is not None:
         # forward Euler conserves enthalpy to first order only: two valid
@@ -102,6 +125,17 @@ def _full(gpu, ref, spread_Y, spread_T, mech=None, T0=None, Y0=None, y_step_max=
                        np.sum(np.abs(Yo - rY) * np.abs(hWg), axis=1)) / cpg
     overT = np.nonzero(dT > limT)[0]
     assert overT.size == 0, "cells beyond the T bound: %s dT %s" % (overT[:8], dT[overT[:8]])
+    ratio = dY / np.maximum(spread_Y, 1e-300)
+    print("|dY| / probe envelope: median %.3g p99 %.3g max %.3g (outside the %d allowed cells)"
+          % (np.median(ratio), np.percentile(ratio, 99),
+             np.delete(ratio, bad).max() if ratio.size > bad.size else 0.0, bad.size))
+    if runs is not None:
+        keep = np.ones(len(dY), bool)
+        keep[bad] = False
+        _distribution(dY, [r[0] for r in runs.values()], keep & (spread_Y >= 1e-2 * TOL_Y),
+                      "|dY|")
+        _distribution(dT, [r[1] for r in runs.values()], keep & (spread_T >= 1e-2 * TOL_T),
+                      "|dT|")
     return dict(well=well.mean(), within_bar=np.mean((dY <= TOL_Y) & (dT <= TOL_T)),
                 max_dY_well=dY[well].max() if well.any() else 0.0, max_dY=dY.max(),
                 max_dT=dT.max(), iter_match=np.mean(it == rit))
@@ -111,14 +145,15 @@ def _full(gpu, ref, spread_Y, spread_T, mech=None, T0=None, Y0=None, y_step_max=
 @pytest.fixture(scope="module")
 def small():
     mech, T, P, Y, dt = synth.small_case(4096)
-    base, sY, sT = oracle.conditioning(mech, T, P, Y, dt)
-    return mech, T, P, Y, dt, base, sY, sT
+    runs = {}
+    base, sY, sT = oracle.conditioning(mech, T, P, Y, dt, per_run=runs)
+    return mech, T, P, Y, dt, base, sY, sT, runs
 
 
 def test_small_full_solve(small):
-    mech, T, P, Y, dt, ref, sY, sT = small
+    mech, T, P, Y, dt, ref, sY, sT, runs = small
     gpu = _gpu_solve(mech, T, P, Y, dt)
-    r = _full(gpu, ref, sY, sT, mech, T, Y)
+    r = _full(gpu, ref, sY, sT, mech, T, Y, runs=runs)
     print("8/20 x 4096:", {k: float("%.4g" % v) for k, v in r.items()})
     # conservation on the GPU result itself
     np.testing.assert_allclose(gpu[1].sum(axis=1), Y.sum(axis=1), rtol=0, atol=1e-12)
@@ -139,7 +174,7 @@ def test_small_prefix(small, k):
 
 @pytest.mark.parametrize("n", [1, 31, 33, 1000])
 def test_ragged_sizes(small, n):
-    mech, T, P, Y, dt, ref, sY, sT = small
+    mech, T, P, Y, dt, ref, sY, sT, _ = small
     gpu = _gpu_solve(mech, T[:n], P[:n], Y[:n], dt)
     _full(gpu, tuple(r[:n] for r in ref), sY[:n], sT[:n], mech, T[:n], Y[:n], min_well=0.0)
 
@@ -198,6 +233,9 @@ def test_maxiter_status_mix(small):
 
 
 # -------------------------------------------------- 32 / 150 and 53 / 325
+# Short step prefixes here, at the 1e-10 bar; full solves and prefixes of 50,
+# 100 and 200 steps on the 32/150 workload against the oracle's stored probe
+# runs are in test_gpu_scale_parity.
 @pytest.fixture(scope="module")
 def scale():
     mech = synth.scale_mechanism()
@@ -212,15 +250,6 @@ def test_scale_prefix(scale, k):
     ref = oracle.solve(mech, T, P, Y, dt, max_iters=k)
     gpu = _gpu_solve(mech, T, P, Y, dt, max_iters=k)
     _prefix(gpu, ref, k)
-
-
-def test_scale_full_solve(scale):
-    mech, T, P, Y, dt = scale
-    base, sY, sT = oracle.conditioning(mech, T, P, Y, dt)
-    gpu = _gpu_solve(mech, T, P, Y, dt)
-    r = _full(gpu, base, sY, sT, mech, T, Y, min_well=0.0)
-    print("32/150 x 192:", {k: float("%.4g" % v) for k, v in r.items()})
-    np.testing.assert_allclose(gpu[1].sum(axis=1), Y.sum(axis=1), rtol=0, atol=1e-11)
 
 
 @pytest.mark.parametrize("k", [1, 14, 20])

@@ -6,20 +6,23 @@ max|dY| <= 1e-4 and |dT| <= 0.5 K.  As for the FP64 path (test_gpu_fp64),
 STEV's final state is ill-conditioned on ringing cells, so the target is
 required on every cell that the oracle's single-precision-sized conditioning
 probe (kf changed by 2^-22, K by 2^-18, the limiter and ringing thresholds by
-2^-22) leaves within 1e-6 / 1e-3 K, and the
-rest must stay within the validity bounds of test_gpu_fp64 (twice the
-limiter's per-step bound, the first-order enthalpy drift)."""
+2^-22) leaves within 1e-6 / 1e-3 K; every other cell must lie within the
+target plus 100 times that probe's spread (T also within the first-order
+enthalpy drift of test_gpu_fp64), and where the probe runs are given, the
+deviations over the ill-conditioned cells must be distributed like one probe
+run's (median, 90th and 99th percentiles within 4x of the largest probe's)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1905_09395_b300 import MIXED, Mechanism, synth
-from test_gpu_fp64 import _enthalpy
+from test_gpu_fp64 import _distribution, _enthalpy
 
 pytestmark = pytest.mark.gpu
 
 TOL_Y, TOL_T = 1e-4, 0.5
 WELL_Y, WELL_T = 1e-6, 1e-3
+ENVELOPE = 100.0   # elsewhere: |gpu - oracle| <= target + ENVELOPE * probe spread
 
 
 def _solve(mech, T, P, Y, dt, **opts):
@@ -31,10 +34,13 @@ def _solve(mech, T, P, Y, dt, **opts):
     return out
 
 
-def _check(mech, T0, Y0, gpu, ref, sY, sT, label, outliers=0.0, outlier_cap=None):
+def _check(mech, T0, Y0, gpu, ref, sY, sT, label, outliers=0.0, outlier_cap=None, runs=None):
     """outliers: fraction of well-conditioned cells allowed over the target,
     each still within outlier_cap = (dY, dT) (for approximations such as the
-    thermo network, whose error is systematic rather than rounding-sized)."""
+    thermo network, whose error is systematic rather than rounding-sized, and
+    for the exact equilibrium cancellation of test_gpu_bfer).  runs: the
+    probe runs' own deviations (oracle.conditioning's per_run), for the
+    distribution check."""
     To, Yo, it, st = gpu
     rT, rY, rit, rst = ref
     assert (st == rst).all(), "status differs in %d cells" % int((st != rst).sum())
@@ -48,21 +54,34 @@ def _check(mech, T0, Y0, gpu, ref, sY, sT, label, outliers=0.0, outlier_cap=None
     if bad.size:
         assert np.all(dY[bad] <= outlier_cap[0]) and np.all(dT[bad] <= outlier_cap[1]), (
             "outliers beyond their cap: dY %s dT %s" % (dY[bad].max(), dT[bad].max()))
-    assert np.all(dY <= np.maximum(TOL_Y + 100 * sY, 2e-3)), "Y beyond validity bound"
+    keep = np.ones(len(dY), bool)
+    keep[bad] = False
+    limY = TOL_Y + ENVELOPE * sY
+    over = np.nonzero(keep & (dY > limY))[0]
+    assert over.size == 0, "Y beyond the probes' envelope: cells %s dY %s spread %s" % (
+        over[:8], dY[over[:8]], sY[over[:8]])
     H0, _, _ = _enthalpy(mech, T0, Y0)
     Hg, cpg, hWg = _enthalpy(mech, To, Yo)
     Ho, _, _ = _enthalpy(mech, rT, rY)
-    limT = TOL_T + 100 * sT + (np.abs(Hg - H0) + np.abs(Ho - H0) +
-                               np.sum(np.abs(Yo - rY) * np.abs(hWg), axis=1)) / cpg
-    assert np.all(dT <= limT), "T beyond validity bound"
+    limT = TOL_T + ENVELOPE * sT + (np.abs(Hg - H0) + np.abs(Ho - H0) +
+                                    np.sum(np.abs(Yo - rY) * np.abs(hWg), axis=1)) / cpg
+    overT = np.nonzero(keep & (dT > limT))[0]
+    assert overT.size == 0, "T beyond its bound: cells %s dT %s" % (overT[:8], dT[overT[:8]])
+    if runs is not None:
+        _distribution(dY, [r[0] for r in runs.values()], keep & (sY >= 1e-2 * TOL_Y),
+                      label + " |dY|")
+        _distribution(dT, [r[1] for r in runs.values()], keep & (sT >= 1e-2 * TOL_T),
+                      label + " |dT|")
     # FP32 production rates sum to zero only to single precision (~1e-7
     # relative per step), so sum Y drifts by far less than the target
     np.testing.assert_allclose(Yo.sum(axis=1), Y0.sum(axis=1), rtol=0, atol=1e-6)
     within = np.mean((dY <= TOL_Y) & (dT <= TOL_T))
     print("%s: well-conditioned %.3f, within target %.4f (well-conditioned %.4f), max dY %.3g"
-          " (well %.3g), max dT %.3g, iteration match %.3f"
+          " (well %.3g), max dT %.3g, iteration match %.3f, max (|dY| - target) / envelope %.3g"
           % (label, well.mean(), within, 1.0 - bad.size / max(well.sum(), 1), dY.max(),
-             dY[well].max() if well.any() else 0, dT.max(), np.mean(it == rit)))
+             dY[well].max() if well.any() else 0, dT.max(), np.mean(it == rit),
+             ((dY[keep] - TOL_Y).clip(0) / np.maximum(sY[keep], 1e-300)).max()
+             if keep.any() else 0.0))
     return within
 
 
@@ -71,7 +90,7 @@ def test_mixed_small_case(lanes):
     mech, T, P, Y, dt = synth.small_case(2048)
     ref, sY, sT = _small_conditioning()
     within = _check(mech, T, Y, _solve(mech, T, P, Y, dt, lanes_per_cell=lanes), ref, sY, sT,
-                    "mixed 8/20 x 2048, lanes %d" % lanes)
+                    "mixed 8/20 x 2048, lanes %d" % lanes, runs=_small_runs())
     assert within > 0.95
 
 
@@ -81,19 +100,15 @@ _cache = {}
 def _small_conditioning():
     if "small" not in _cache:
         mech, T, P, Y, dt = synth.small_case(2048)
-        _cache["small"] = oracle.conditioning(mech, T, P, Y, dt, level="fp32")
+        runs = {}
+        _cache["small"] = oracle.conditioning(mech, T, P, Y, dt, level="fp32", per_run=runs)
+        _cache["small_runs"] = runs
     return _cache["small"]
 
 
-def test_mixed_scale_mechanism():
-    # on the 32/150 workload nearly every cell is ill-conditioned even at the
-    # FP64 level (test_gpu_fp64), so only the validity bounds are checked
-    mech = synth.scale_mechanism()
-    T, P, Y = synth.make_cells(mech, 96, seed=11, T_range=(800, 2200), P_atm_range=(1, 5),
-                               dirichlet=0.5)
-    ref = oracle.solve(mech, T, P, Y, 1e-3)
-    z = np.zeros(len(T))
-    _check(mech, T, Y, _solve(mech, T, P, Y, 1e-3), ref, z + 1.0, z + 1.0, "mixed 32/150 x 96")
+def _small_runs():
+    _small_conditioning()
+    return _cache["small_runs"]
 
 
 @pytest.mark.parametrize("k", [1, 14, 50])
