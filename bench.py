@@ -677,8 +677,8 @@ def run_bfer(args):
             fp64 = name == "plain_fp64"
             a["oracle_error"] = oracle_error(head, keep["ref"], 1e-8 if fp64 else 1e-4,
                                              1e-6 if fp64 else 0.5)
-    # the value is the mixed-precision polynomial arm: the network kernel runs
-    # one cell per warp, which leaves most lanes idle on a 6-species mechanism
+    # the value is the mixed-precision polynomial arm: on a 6-species
+    # mechanism the polynomials cost far less than the network's MMAs
     h = arms["mixed_poly"]
     line = {"metric": "cell-solves/s, BFER methane mechanism (Sec. 7.1), random fixed states, "
                       "t_f = 1 ms", "value": h["value"], "value_arm": "mixed_poly",
