@@ -96,7 +96,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 // Instruction descriptor of kind::tf32: D in FP32, A and B TF32, both
-// K-major, N = M = 128.
+// K-major, M = 128, N = 256.
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
                                 ((uint32_t)(kTile >> 4) << 24);
 
@@ -285,15 +285,17 @@ __global__ void rows_dot_kernel(const float* __restrict__ X, long long n, long l
 }
 
 // y = (A + lambda diag(A) + eps I) p, one warp per row (A symmetric, row-major).
+// vec: the rows of A are 16-byte aligned (A aligned, lda a multiple of 4) and
+// are read as float4 (p, a work array, always is).
 __global__ void damped_symv_kernel(const float* __restrict__ A, long long n, long long lda,
                                    float lambda, float eps, const float* __restrict__ p,
-                                   float* __restrict__ y) {
+                                   float* __restrict__ y, bool vec) {
   const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const float* a = A + row * lda;
   float acc = 0.0f;
-  const long long n4 = (lda % 4 == 0) ? (n / 4) * 4 : 0;
+  const long long n4 = vec ? (n / 4) * 4 : 0;
   for (long long j = (long long)lane * 4; j < n4; j += 128) {
     const float4 v = *reinterpret_cast<const float4*>(a + j);
     const float4 q = *reinterpret_cast<const float4*>(p + j);
@@ -442,6 +444,7 @@ stev_status damped_cg(const float* A, long long n, long long lda, const float* b
   if (n < 1 || lda < n || max_iters < 1 || !(rtol > 0.0))
     return fail(STEV_EINVAL, "damped_cg: bad arguments");
   const float lam = (float)lambda, ep = (float)eps;
+  const bool vec = lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
   const unsigned vb = (unsigned)((n + 255) / 256), mb = (unsigned)((n * 32 + 255) / 256);
   float *r = w->r, *z = w->z, *p = w->p, *q = w->q;
   double* part = w->part;
@@ -470,7 +473,7 @@ stev_status damped_cg(const float* A, long long n, long long lda, const float* b
   int it = 0;
   if (r0 > 0.0) {
     for (it = 0; it < max_iters; ++it) {
-      lm::damped_symv_kernel<<<mb, 256, 0, s>>>(A, n, lda, lam, ep, p, q);
+      lm::damped_symv_kernel<<<mb, 256, 0, s>>>(A, n, lda, lam, ep, p, q, vec);
       CG_TRY(dot(p, q, nullptr));
       const double pq = hd[0];
       if (!(pq > 0.0)) break;  // not positive along p: stop with the current x
