@@ -68,14 +68,15 @@ stev_status rows_dot(const float* X, long long n, long long k, long long ldx, co
 // Work arrays of damped_cg for systems of n unknowns.
 struct CgWork {
   float *r, *z, *p, *q;
-  double *part, *dd;
+  double* part;
+  void* state;  // the solver's scalars on the device (lm::CgState)
 };
 stev_status cg_work_alloc(CgWork* w, long long n);
 void cg_work_free(CgWork* w);
 // (A + lambda diag(A) + eps I) x = b by conjugate gradients with the Jacobi
 // preconditioner, A symmetric [n][lda]; stops when the residual has fallen by
-// rtol or after max_iters; *iters gets the iterations taken.  Synchronises s
-// once per iteration (the step lengths are computed on the host).
+// rtol or after max_iters; *iters gets the iterations taken.  The step
+// lengths are computed on the device; s is synchronised once per 16 steps.
 stev_status damped_cg(const float* A, long long n, long long lda, const float* b, double lambda,
                       double eps, float* x, int max_iters, double rtol, int* iters, CgWork* w,
                       cudaStream_t s);

@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -284,12 +285,25 @@ __global__ void rows_dot_kernel(const float* __restrict__ X, long long n, long l
   if (lane == 0) g[row] = acc;
 }
 
+// The conjugate-gradient solver's scalars live on the device, so that its
+// steps are queued without a host round trip each: every kernel of a step
+// reads `done` first and does nothing once the solve has stopped.
+struct CgState {
+  double rz;     // r . z of the current direction
+  double r0;     // |r| at the start
+  double rtol;   // stop once |r| <= rtol r0
+  float alpha, beta;
+  int done;      // converged, or a direction of non-positive curvature
+  int it;        // steps completed
+};
+
 // y = (A + lambda diag(A) + eps I) p, one warp per row (A symmetric, row-major).
 // vec: the rows of A are 16-byte aligned (A aligned, lda a multiple of 4) and
 // are read as float4 (p, a work array, always is).
 __global__ void damped_symv_kernel(const float* __restrict__ A, long long n, long long lda,
                                    float lambda, float eps, const float* __restrict__ p,
-                                   float* __restrict__ y, bool vec) {
+                                   float* __restrict__ y, bool vec, const CgState* cs) {
+  if (cs->done) return;
   const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -310,12 +324,14 @@ __global__ void damped_symv_kernel(const float* __restrict__ A, long long n, lon
   if (lane == 0) y[row] = acc + (lambda * a[row] + eps) * p[row];
 }
 
-// Partial dot products in FP64, one per block (fixed order), then summed by
-// dot_finish in block order: out[0] = sum x y (and out[1] = sum x z if z).
+// Partial dot products in FP64, one per block (fixed order), then summed in
+// block order by the step kernels below: part[2b] = sum x y, part[2b + 1] =
+// sum x z (if z).
 constexpr int kDotBlocks = 256, kDotThreads = 256;
 __global__ void dot_partial_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                    const float* __restrict__ z, long long n,
-                                   double* __restrict__ part) {
+                                   double* __restrict__ part, const CgState* cs) {
+  if (cs->done) return;
   __shared__ double s0[kDotThreads], s1[kDotThreads];
   double a = 0.0, b = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -338,28 +354,66 @@ __global__ void dot_partial_kernel(const float* __restrict__ x, const float* __r
     part[2 * blockIdx.x + 1] = s1[0];
   }
 }
-__global__ void dot_finish_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      a += part[2 * i];
-      b += part[2 * i + 1];
-    }
-    out[0] = a;
-    out[1] = b;
+__device__ __forceinline__ void sum_parts(const double* part, int nb, double& a, double& b) {
+  a = 0.0;
+  b = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
   }
+}
+// start: rz = r . z, r0 = |r| (part from dot(r, z, r)); nothing to do if r0 = 0
+__global__ void cg_start_kernel(const double* __restrict__ part, int nb, double rtol,
+                                CgState* cs) {
+  if (threadIdx.x != 0) return;
+  double a, b;
+  sum_parts(part, nb, a, b);
+  cs->rz = a;
+  cs->r0 = sqrt(b);
+  cs->rtol = rtol;
+  cs->it = 0;
+  cs->done = !(cs->r0 > 0.0);
+}
+// alpha = rz / (p . q) (part from dot(p, q)); stop on non-positive curvature
+__global__ void cg_alpha_kernel(const double* __restrict__ part, int nb, CgState* cs) {
+  if (threadIdx.x != 0 || cs->done) return;
+  double pq, unused;
+  sum_parts(part, nb, pq, unused);
+  if (!(pq > 0.0)) {
+    cs->done = 1;  // stop with the current x
+    return;
+  }
+  cs->alpha = (float)(cs->rz / pq);
+}
+// after the update: rz' = r . z, |r| (part from dot(r, z, r)); the step is
+// complete; stop once |r| <= rtol r0, else beta = rz' / rz
+__global__ void cg_beta_kernel(const double* __restrict__ part, int nb, CgState* cs) {
+  if (threadIdx.x != 0 || cs->done) return;
+  double rz1, rr;
+  sum_parts(part, nb, rz1, rr);
+  cs->it += 1;
+  if (sqrt(rr) <= cs->rtol * cs->r0) {
+    cs->done = 1;
+    return;
+  }
+  cs->beta = (float)(rz1 / cs->rz);
+  cs->rz = rz1;
 }
 
 // z = r / m, m = diag(A)(1 + lambda) + eps (the Jacobi preconditioner)
 __global__ void precond_kernel(const float* __restrict__ A, long long n, long long lda, float lambda,
-                               float eps, const float* __restrict__ r, float* __restrict__ z) {
+                               float eps, const float* __restrict__ r, float* __restrict__ z,
+                               const CgState* cs) {
+  if (cs->done) return;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) z[i] = r[i] / (A[i * lda + i] * (1.0f + lambda) + eps);
 }
 // x += alpha p; r -= alpha q
-__global__ void cg_update_kernel(long long n, float alpha, const float* __restrict__ p,
+__global__ void cg_update_kernel(long long n, const float* __restrict__ p,
                                  const float* __restrict__ q, float* __restrict__ x,
-                                 float* __restrict__ r) {
+                                 float* __restrict__ r, const CgState* cs) {
+  if (cs->done) return;
+  const float alpha = cs->alpha;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     x[i] = fmaf(alpha, p[i], x[i]);
@@ -367,8 +421,10 @@ __global__ void cg_update_kernel(long long n, float alpha, const float* __restri
   }
 }
 // p = z + beta p
-__global__ void cg_direction_kernel(long long n, float beta, const float* __restrict__ z,
-                                    float* __restrict__ p) {
+__global__ void cg_direction_kernel(long long n, const float* __restrict__ z,
+                                    float* __restrict__ p, const CgState* cs) {
+  if (cs->done) return;
+  const float beta = cs->beta;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = fmaf(beta, p[i], z[i]);
 }
@@ -448,51 +504,44 @@ stev_status damped_cg(const float* A, long long n, long long lda, const float* b
   const unsigned vb = (unsigned)((n + 255) / 256), mb = (unsigned)((n * 32 + 255) / 256);
   float *r = w->r, *z = w->z, *p = w->p, *q = w->q;
   double* part = w->part;
-  double* dd = w->dd;
-  double hd[2];
-  auto dot = [&](const float* u, const float* v, const float* t) -> cudaError_t {
-    lm::dot_partial_kernel<<<lm::kDotBlocks, lm::kDotThreads, 0, s>>>(u, v, t, n, part);
-    lm::dot_finish_kernel<<<1, 32, 0, s>>>(part, lm::kDotBlocks, dd);
-    cudaError_t e = cudaMemcpyAsync(hd, dd, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return e;
-  };
+  lm::CgState* cs = static_cast<lm::CgState*>(w->state);
+  lm::CgState h{};
 #define CG_TRY(expr)                                                                        \
   do {                                                                                      \
     const cudaError_t e_ = (expr);                                                          \
     if (e_ != cudaSuccess) return fail(STEV_ECUDA, "damped_cg: %s", cudaGetErrorString(e_)); \
   } while (0)
-  // x = 0, r = b, z = M^-1 r, p = z
+  // x = 0, r = b, z = M^-1 r, p = z; rz and r0 on the device
+  CG_TRY(cudaMemsetAsync(cs, 0, sizeof(lm::CgState), s));
   CG_TRY(cudaMemsetAsync(x, 0, (size_t)n * 4, s));
   CG_TRY(cudaMemcpyAsync(r, b, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-  lm::precond_kernel<<<vb, 256, 0, s>>>(A, n, lda, lam, ep, r, z);
+  lm::precond_kernel<<<vb, 256, 0, s>>>(A, n, lda, lam, ep, r, z, cs);
   CG_TRY(cudaMemcpyAsync(p, z, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-  CG_TRY(dot(r, z, r));
-  double rz = hd[0];
-  const double r0 = std::sqrt(hd[1]);
-  int it = 0;
-  if (r0 > 0.0) {
-    for (it = 0; it < max_iters; ++it) {
-      lm::damped_symv_kernel<<<mb, 256, 0, s>>>(A, n, lda, lam, ep, p, q, vec);
-      CG_TRY(dot(p, q, nullptr));
-      const double pq = hd[0];
-      if (!(pq > 0.0)) break;  // not positive along p: stop with the current x
-      const float alpha = (float)(rz / pq);
-      lm::cg_update_kernel<<<vb, 256, 0, s>>>(n, alpha, p, q, x, r);
-      lm::precond_kernel<<<vb, 256, 0, s>>>(A, n, lda, lam, ep, r, z);
-      CG_TRY(dot(r, z, r));
-      const double rz1 = hd[0];
-      if (std::sqrt(hd[1]) <= rtol * r0) {
-        ++it;
-        break;
-      }
-      lm::cg_direction_kernel<<<vb, 256, 0, s>>>(n, (float)(rz1 / rz), z, p);
-      rz = rz1;
+  lm::dot_partial_kernel<<<lm::kDotBlocks, lm::kDotThreads, 0, s>>>(r, z, r, n, part, cs);
+  lm::cg_start_kernel<<<1, 32, 0, s>>>(part, lm::kDotBlocks, rtol, cs);
+  // steps queued kCgBatch at a time; the host reads the state once per batch
+  // (a step queued after the solve stopped does nothing)
+  constexpr int kCgBatch = 16;
+  int queued = 0;
+  do {
+    const int k = std::min(kCgBatch, max_iters - queued);
+    for (int j = 0; j < k; ++j) {
+      lm::damped_symv_kernel<<<mb, 256, 0, s>>>(A, n, lda, lam, ep, p, q, vec, cs);
+      lm::dot_partial_kernel<<<lm::kDotBlocks, lm::kDotThreads, 0, s>>>(p, q, nullptr, n, part, cs);
+      lm::cg_alpha_kernel<<<1, 32, 0, s>>>(part, lm::kDotBlocks, cs);
+      lm::cg_update_kernel<<<vb, 256, 0, s>>>(n, p, q, x, r, cs);
+      lm::precond_kernel<<<vb, 256, 0, s>>>(A, n, lda, lam, ep, r, z, cs);
+      lm::dot_partial_kernel<<<lm::kDotBlocks, lm::kDotThreads, 0, s>>>(r, z, r, n, part, cs);
+      lm::cg_beta_kernel<<<1, 32, 0, s>>>(part, lm::kDotBlocks, cs);
+      lm::cg_direction_kernel<<<vb, 256, 0, s>>>(n, z, p, cs);
     }
-  }
-  CG_TRY(cudaGetLastError());
+    queued += k;
+    CG_TRY(cudaGetLastError());
+    CG_TRY(cudaMemcpyAsync(&h, cs, sizeof h, cudaMemcpyDeviceToHost, s));
+    CG_TRY(cudaStreamSynchronize(s));
+  } while (!h.done && queued < max_iters);
 #undef CG_TRY
-  if (iters) *iters = it;
+  if (iters) *iters = h.it;
   return STEV_OK;
 }
 
@@ -554,8 +603,8 @@ stev_status cg_work_alloc(CgWork* w, long long n) {
   w->p = dev_alloc<float>((size_t)n);
   w->q = dev_alloc<float>((size_t)n);
   w->part = dev_alloc<double>(2 * lm::kDotBlocks);
-  w->dd = dev_alloc<double>(2);
-  if (!w->r || !w->z || !w->p || !w->q || !w->part || !w->dd) {
+  w->state = dev_alloc<lm::CgState>(1);
+  if (!w->r || !w->z || !w->p || !w->q || !w->part || !w->state) {
     cg_work_free(w);
     return fail(STEV_ENOMEM, "cudaMalloc failed (conjugate-gradient work arrays)");
   }
@@ -567,7 +616,7 @@ void cg_work_free(CgWork* w) {
   cudaFree(w->p);
   cudaFree(w->q);
   cudaFree(w->part);
-  cudaFree(w->dd);
+  cudaFree(w->state);
   *w = CgWork{};
 }
 }  // namespace host
