@@ -29,10 +29,11 @@ namespace stev {
 
 // One STEV iteration of one cell by its group (Secs. 2.1-2.3, Eq. 18).
 // Returns -1 to continue, else the STEV_CELL_* outcome.
-template <int G>
+template <int G, int kWin>
 __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, double* cY, double* cC,
                                          double* cG, double* cH, double* cQ, double* cHist,
-                                         double* cRof, int l, CellState& st) {
+                                         double* cRof, int l, CellState& st, double* win_s,
+                                         double* win_a) {
   const int S = L.S, R = L.R, Rrev = L.Rrev, N = L.dft_n;
   const double T = st.T;
   const double lnT = log(T);
@@ -139,23 +140,41 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
   const bool last = (h >= st.t_rem);
   if (last) h = st.t_rem;
 
-  // DFT ringing detection and damping (Eqs. 8-13) on reversible reactions
+  // DFT ringing detection and damping (Eqs. 8-13) on reversible reactions.
+  // Eq. 9's D0 = |sum of the window| and the sum of |x| of Eq. 10's bound:
+  // for a lane's first kWin rows kept as running sums in registers (the tap
+  // that leaves at the next step, still in its slot now, comes off them after
+  // this step's decision, the new tap goes on at the next step), recomputed
+  // from the N taps once per window (the first full step and every N steps
+  // after), so their drift stays within a window's roundings; elsewhere summed
+  // directly from the taps in storage order.
   if (L.dft_on) {
     const bool full = (st.nhist + 1 >= N);
-    for (int w = l; w < Rrev; w += G) {
+    const bool refresh = (st.nhist + 1) % N == 0;
+    const int knext = (ktap + 1) % N;
+    auto damp = [&](int w, bool running, double& ws, double& wa) {
       const double x = cHist[ktap * Rrev + w] * h;
       cHist[ktap * Rrev + w] = x;
       double rof = cRof[w];
       if (full) {
-        double s = 0.0;
-        for (int m = 0; m < N; ++m) s += cHist[m * Rrev + w];  // storage order, as Eq. 9's sum
+        double s = 0.0, a = 0.0;
+        bool have_a = false;
+        if (running && !refresh) {
+          s = ws + x;
+          a = wa + fabs(x);
+          have_a = true;
+        } else {
+          for (int m = 0; m < N; ++m) s += cHist[m * Rrev + w];  // storage order, as Eq. 9's sum
+        }
         const double D0 = fabs(s);
         double rstar = L.r_fac;
         if (D0 < L.tol_freq) {  // only then can Eq. 12 damp
           // every |X_j| <= sum |x_m|: a window with D0 >= Tol_ring sum|x_m|
           // cannot ring (Eq. 10), so its high bins are not needed
-          double a = 0.0;
-          for (int m = 0; m < N; ++m) a += fabs(cHist[m * Rrev + w]);
+          if (!have_a) {
+            for (int m = 0; m < N; ++m) a += fabs(cHist[m * Rrev + w]);
+            have_a = true;
+          }
           if (D0 < L.tol_ring * a) {
             // D0 < Tol_ring max|X_j|, compared as squares in units of sum|x_m|
             // (every scaled magnitude is <= 1, so the squares cannot underflow)
@@ -185,11 +204,25 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
           }
         }
         rof = fmax(fmin(rof * rstar, 1.0), L.rof_min);
+        if (running) {
+          if (!have_a)
+            for (int m = 0; m < N; ++m) a += fabs(cHist[m * Rrev + w]);
+          const double xl = cHist[knext * Rrev + w];  // leaves the window next step
+          ws = s - xl;
+          wa = a - fabs(xl);
+        }
       } else {
         rof = fmin(rof * L.r_fac, 1.0);
       }
       cRof[w] = rof;
+    };
+    double unused_s = 0.0, unused_a = 0.0;
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) {
+      const int w = l + G * j;
+      if (w < Rrev) damp(w, true, win_s[j], win_a[j]);
     }
+    for (int w = l + G * kWin; w < Rrev; w += G) damp(w, false, unused_s, unused_a);
     st.nhist += 1;
   }
 
@@ -213,8 +246,18 @@ __device__ __forceinline__ int step_fp64(const Launch& L, const Tables& tb, doub
 }
 
 // ---------------------------------------------------------- persistent kernel
+// Reversible reactions per lane whose damper window sums are kept running in
+// registers (step_fp64): the first five of each lane with 32-lane groups,
+// whose cells (19 KB each on 32/150) leave at most 12 per CTA, so the block
+// bound of 384 threads gives the registers (170 per thread) for them.
 template <int G>
-__global__ void __launch_bounds__(kMaxBlock, 1) stev_fp64_kernel(Launch L) {
+struct Fp64Win {
+  static constexpr int n = G == 32 ? 5 : 0;
+  static constexpr int block = G == 32 ? 384 : kMaxBlock;
+};
+
+template <int G>
+__global__ void __launch_bounds__(Fp64Win<G>::block, 1) stev_fp64_kernel(Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = L.S, R = L.R;
   // stage the mechanism tables once per CTA
@@ -276,6 +319,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) stev_fp64_kernel(Launch L) {
   unsigned idle_sleep = 1000u;        // serving: ns between looks while idle
   int serve_skip = 0;                 // serving: steps before the next look
   bool exhausted = false;  // warp-uniform
+  // the damper's running window sums (Fp64Win; rewritten at a cell's first
+  // full window before they are read)
+  constexpr int kWin = Fp64Win<G>::n;
+  double win_s[kWin > 0 ? kWin : 1], win_a[kWin > 0 ? kWin : 1];
+#pragma unroll
+  for (int j = 0; j < (kWin > 0 ? kWin : 1); ++j) win_s[j] = win_a[j] = 0.0;
   while (true) {
     long long c = -1;
     if (!L.serve) {
@@ -327,7 +376,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) stev_fp64_kernel(Launch L) {
     }
     idle_since = 0;
     idle_sleep = 1000u;
-    const int outcome = step_fp64<G>(L, tb, cY, cC, cG, cH, cQ, cHist, cRof, l, st);
+    const int outcome = step_fp64<G, Fp64Win<G>::n>(L, tb, cY, cC, cG, cH, cQ, cHist, cRof, l, st,
+                                                    win_s, win_a);
     if (st.cell >= 0 && outcome >= 0) {
       const CellIO io = cell_io(L, st.b);
       const long long c = st.lc;
