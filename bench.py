@@ -49,7 +49,7 @@ N_SMS = 148
 # profiles/ (reads only: the small cases' output writes stay in L2), scaled to
 # the full launch by the cells it processes.  None when the kernel changed
 # after its capture.
-DRAM_BYTES_PER_CELL = {"mixed": 966656 / 3256, "fp64": 865536 / 1628, "mixed+mlp": 979456 / 3256}
+DRAM_BYTES_PER_CELL = {"mixed": 966656 / 3256, "fp64": 612608 / 1628, "mixed+mlp": 979456 / 3256}
 
 
 def bf16_tflops(burst: bool = False) -> tuple:
